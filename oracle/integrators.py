@@ -1,0 +1,195 @@
+"""MD schedules and the HMC trajectory (Sec. 2 of arXiv:1512.03812).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).  Every schedule is
+written as the literal composition printed in the paper, with no merging of
+consecutive kicks, so that the inversion counter reproduces the paper's
+"D^{-1} per step" (Sec. 3, end).
+
+Primitives (Sec. 2.1, the discrete updates e^{hA} and e^{hB}):
+  drift  e^{eps A}: U -> exp(i eps P) U, i.e. q <- q + eps p
+  kick   e^{eps B}: P -> P - eps F; for U(1) the momenta are real and the
+         factor i of the Lie-algebra notation is dropped: p <- p - eps F
+  fg     e^{(2/3) h B + h^3/72 C}: p <- p - (2h/3) F + (h^3/72) C, with
+         C = grad |F|^2 of Eq. force_gradient.  This is the sign that gives
+         fourth order (the paper prints both signs, Eq. 5stage_fg versus
+         Eq. 5stage_multi_fg).  ``fg='shifted'`` replaces F and C by the
+         force at the shifted field q - (h^2/24) F(q).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import schwinger as sw
+
+
+@dataclass
+class State:
+    lat: sw.Lattice
+    q: np.ndarray
+    p: np.ndarray
+    phi: np.ndarray
+    solver: sw.Solver
+
+
+def drift(st: State, eps: float) -> None:
+    st.q = st.q + eps * st.p
+
+
+def kick(st: State, eps: float, part: str) -> None:
+    st.p = st.p - eps * sw.force(st.lat, sw.links(st.q), st.phi, st.solver, part)
+
+
+def fg_kick(st: State, h: float, part: str, fg: str) -> None:
+    """The force-gradient kick e^{(2/3) h B + (1/72) h^3 C} for step h."""
+    if fg == "exact":
+        F, C = sw.force_and_gradient(st.lat, sw.links(st.q), st.phi, st.solver, part)
+        st.p = st.p - (2.0 * h / 3.0) * F + (h ** 3 / 72.0) * C
+    elif fg == "shifted":
+        st.p = st.p - (2.0 * h / 3.0) * sw.shifted_force(st.lat, st.q, st.phi, st.solver, h, part)
+    else:
+        raise ValueError(fg)
+
+
+# ----------------------------------------------------------- basic schemes --
+
+def leapfrog(st: State, h: float, **_) -> None:
+    """Delta(h) = e^{hB/2} e^{hA} e^{hB/2} (Eq. leap)."""
+    kick(st, h / 2, "full")
+    drift(st, h)
+    kick(st, h / 2, "full")
+
+
+def five_stage(st: State, h: float, lam: float = 1.0 / 6.0, **_) -> None:
+    """Delta_5(h) = e^{lam h B} e^{h A/2} e^{(1-2 lam) h B} e^{h A/2} e^{lam h B}
+    (Eq. 5stage prints lam = 1/6)."""
+    kick(st, lam * h, "full")
+    drift(st, h / 2)
+    kick(st, (1 - 2 * lam) * h, "full")
+    drift(st, h / 2)
+    kick(st, lam * h, "full")
+
+
+def five_stage_fg(st: State, h: float, fg: str = "exact", **_) -> None:
+    """Delta_5C(h) (Eq. 5stage_fg) with the full force gradient C, or its
+    shifted-force approximation (Sec. 2, after Eq. 5stage_fg)."""
+    kick(st, h / 6, "full")
+    drift(st, h / 2)
+    fg_kick(st, h, "full", fg)
+    drift(st, h / 2)
+    kick(st, h / 6, "full")
+
+
+# ---------------------------------------------------------- nested schemes --
+
+def inner_leapfrog(st: State, h: float, M: int) -> None:
+    """Delta_1(h)_M = (e^{h B1/2M} e^{h A/M} e^{h B1/2M})^M (Sec. 2, after
+    Eq. leap_multi); B1 is the gauge action."""
+    for _ in range(M):
+        kick(st, h / (2 * M), "gauge")
+        drift(st, h / M)
+        kick(st, h / (2 * M), "gauge")
+
+
+def inner_fg(st: State, h: float, M: int, fg: str) -> None:
+    """Delta_2(h)_M: M five-stage force-gradient steps of size h/M on the
+    gauge system, C_g = C_GG (Sec. 2, after Eq. 5stage_multi_fg)."""
+    hm = h / M
+    for _ in range(M):
+        kick(st, hm / 6, "gauge")
+        drift(st, hm / 2)
+        fg_kick(st, hm, "gauge", fg)
+        drift(st, hm / 2)
+        kick(st, hm / 6, "gauge")
+
+
+def nested_leapfrog(st: State, h: float, M: int = 1, **_) -> None:
+    """hat Delta(h) = e^{h B2/2} Delta_1(h)_M e^{h B2/2} (Eq. leap_multi)."""
+    kick(st, h / 2, "fermion")
+    inner_leapfrog(st, h, M)
+    kick(st, h / 2, "fermion")
+
+
+def nested_five_stage(st: State, h: float, M: int = 1, lam: float = 1.0 / 6.0, **_) -> None:
+    """hat Delta_5(h) (Eq. 5stage_multi), outer weights lam, 1-2 lam, lam."""
+    kick(st, lam * h, "fermion")
+    inner_leapfrog(st, h / 2, M)
+    kick(st, (1 - 2 * lam) * h, "fermion")
+    inner_leapfrog(st, h / 2, M)
+    kick(st, lam * h, "fermion")
+
+
+def nested_fg(st: State, h: float, M: int = 1, fg: str = "exact", **_) -> None:
+    """hat Delta_5C(h) (Eq. 5stage_multi_fg): C_f = C_FF outside, the
+    force-gradient inner scheme Delta_2 inside."""
+    kick(st, h / 6, "fermion")
+    inner_fg(st, h / 2, M, fg)
+    fg_kick(st, h, "fermion", fg)
+    inner_fg(st, h / 2, M, fg)
+    kick(st, h / 6, "fermion")
+
+
+def adapted_nested_fg(st: State, h: float, M: int = 1, fg: str = "exact", **_) -> None:
+    """tilde Delta_5C(h) (Eq. ad_5stage_multi_fg): C_f = C_FF outside,
+    plain leapfrog Delta_1 inside."""
+    kick(st, h / 6, "fermion")
+    inner_leapfrog(st, h / 2, M)
+    fg_kick(st, h, "fermion", fg)
+    inner_leapfrog(st, h / 2, M)
+    kick(st, h / 6, "fermion")
+
+
+SCHEMES = {
+    "leapfrog": leapfrog,
+    "five_stage": five_stage,
+    "five_stage_fg": five_stage_fg,
+    "nested_leapfrog": nested_leapfrog,
+    "nested_five_stage": nested_five_stage,
+    "nested_fg": nested_fg,
+    "adapted_nested_fg": adapted_nested_fg,
+}
+
+# Omelyan's second-order minimum-norm weight (Omelyan, Mryglod and Folk 2002),
+# used for the "2MN" variant of the five-stage schemes.
+LAMBDA_2MN = 0.1931833275037836
+
+
+def md_trajectory(st: State, scheme: str, tau: float, n: int, M: int = 1,
+                  lam: float = 1.0 / 6.0, fg: str = "exact") -> None:
+    """n steps of size h = tau / n of one scheme."""
+    h = tau / n
+    step = SCHEMES[scheme]
+    for _ in range(n):
+        step(st, h, M=M, lam=lam, fg=fg)
+
+
+@dataclass
+class TrajectoryResult:
+    q: np.ndarray          # links after the Metropolis step
+    q_md: np.ndarray       # links at the end of the MD trajectory
+    p_md: np.ndarray
+    dH: float
+    H0: float
+    H1: float
+    accepted: bool
+
+
+def hmc_trajectory(lat: sw.Lattice, q0: np.ndarray, p0: np.ndarray, eta: np.ndarray,
+                   u: float, scheme: str, tau: float, n: int, M: int = 1,
+                   lam: float = 1.0 / 6.0, fg: str = "exact",
+                   solver: sw.Solver | None = None) -> TrajectoryResult:
+    """One HMC update (Sec. 2.1): pseudofermion heatbath phi = D^dag eta at
+    the starting links, MD trajectory of length tau, Metropolis accept
+    with probability min(1, e^{-Delta H}) decided as u < exp(-Delta H) for
+    a supplied uniform u in [0, 1)."""
+    solver = solver or sw.Solver()
+    phi = sw.apply_D(lat, sw.links(q0), eta, dagger=True)
+    H0 = sw.hamiltonian(lat, q0, p0, phi, solver)
+    st = State(lat, q0.copy(), p0.copy(), phi, solver)
+    md_trajectory(st, scheme, tau, n, M, lam, fg)
+    H1 = sw.hamiltonian(lat, st.q, st.p, phi, solver)
+    dH = H1 - H0
+    accepted = bool(math.isfinite(dH) and (dH <= 0.0 or u < math.exp(-dH)))
+    return TrajectoryResult(st.q if accepted else q0.copy(), st.q, st.p, dH, H0, H1, accepted)
