@@ -1,0 +1,371 @@
+"""Throughput of the Schwinger-model HMC hot path on one GB300 (or N, one
+process per GPU, chains sharded across ranks: weak scaling).
+
+Workload (the mixed-precision versus FP64 configuration of the 64 x 64
+lattice): 64 x 64 sites, beta = 2.0, kappa = 0.26, tau = 1, the adapted
+nested force-gradient scheme (outer n = 8, inner m = 2, exact C_FF),
+FP32 CG with FP64 reliable updates to a true relative residual of 1e-10;
+200 chains per GPU advance one trajectory per step.  The chains start
+from one configuration thermalised by this library's own HMC (untimed);
+every step draws fresh momenta and pseudofermion noise (pre-generated on
+the device before the timed region).
+
+A "step" is one HMC trajectory of every chain: heatbath, H, the MD
+trajectory (all forces, CG solves, force-gradient term, link and momentum
+updates), H, Metropolis.  value = trajectories per second over all ranks.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (one chain's trajectory per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {
+    "workload": "64x64 beta=2.0 kappa=0.26, 200 chains/GPU, adapted nested FG n=8 m=2, "
+                "mixed-precision CG tol 1e-10",
+    "L": 64, "T": 64, "beta": 2.0, "kappa": 0.26, "chains_per_gpu": 200,
+    "scheme": "adapted_nested_fg", "tau": 1.0, "n": 8, "M": 2, "fg": "exact",
+    "cg_tol": 1e-10, "precision": "mixed",
+}
+# algorithmic bytes per site and CG iteration of the FP32 iteration pair
+# (kernel A: r, p, U in, p, t out; kernel B: t, U, p, x, r in, x, r out; 16 B each)
+CG_BYTES_PER_SITE_ITER = {"mixed": (3 + 2) * 16 + (5 + 2) * 16, "f64": (3 + 2) * 32 + (5 + 2) * 32}
+
+
+def kappa_to_m0(k):
+    return 1.0 / (2.0 * k) - 2.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed
+    region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{index}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ our arm ------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1512_03812_gb300 as P
+    from paper_1512_03812_gb300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    P.build()
+
+    W = WORKLOAD
+    B, L, T = args.chains, W["L"], W["T"]
+    m0 = kappa_to_m0(W["kappa"])
+    lat = P.Lattice([L] * B, [T] * B, W["beta"], m0, device=dev)
+    N = lat.N
+    cgp = P.CG(tol=W["cg_tol"], maxit=20000, prec=args.prec)
+    md = P.MD(scheme=W["scheme"], tau=W["tau"], n=W["n"], M=W["M"], fg=W["fg"], cg=cgp)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234 + 7919 * rank)
+
+    def draws(k):
+        p = torch.randn((k, N, 2), generator=gen, device=dev, dtype=torch.float64)
+        e = torch.randn((k, N, 2, 2), generator=gen, device=dev, dtype=torch.float64)
+        e = torch.view_as_complex(e * math.sqrt(0.5)).contiguous()
+        u = torch.rand((k, B), generator=gen, device=dev, dtype=torch.float64).cpu().numpy()
+        return p, e, u
+
+    # thermalise one configuration (chain 0 of a 1-chain lattice), untimed
+    t0 = time.time()
+    one = P.Lattice(L, T, W["beta"], m0, device=dev)
+    q1 = torch.zeros((L * T, 2), dtype=torch.float64, device=dev)
+    g1 = torch.Generator(device=dev)
+    g1.manual_seed(99)
+    md_th = P.MD(scheme="nested_leapfrog", tau=1.0, n=6, M=4, cg=P.CG(1e-8, 20000, "mixed"))
+    acc_th = []
+    for _ in range(args.therm):
+        p = torch.randn((L * T, 2), generator=g1, device=dev, dtype=torch.float64)
+        e = torch.view_as_complex(torch.randn((L * T, 2, 2), generator=g1, device=dev,
+                                              dtype=torch.float64) * math.sqrt(0.5)).contiguous()
+        u = float(torch.rand(1, generator=g1, device=dev, dtype=torch.float64))
+        dH, _, acc = one.hmc_trajectory(q1, p, e, u, md_th)
+        acc_th.append(bool(acc[0]))
+    log(f"thermalised {args.therm} trajectories in {time.time() - t0:.1f}s, acc {np.mean(acc_th):.2f}")
+    q_start = q1.repeat(B, 1).contiguous()
+
+    flush = torch.empty(int(256 * 2 ** 20), dtype=torch.uint8, device=dev)
+
+    def step(q, p, e, u):
+        flush.fill_(1)  # evict the previous step's working set from L2
+        return lat.hmc_trajectory(q, p, e, u, md, check=False)
+
+    q = q_start.clone()
+    pw, ew, uw = draws(args.warmup)
+    for i in range(args.warmup):
+        step(q, pw[i], ew[i], uw[i])
+    torch.cuda.synchronize()
+    del pw, ew
+    K = args.steps
+    pk, ek, uk = draws(K)
+    dHs, accs = [], []
+    binding.profile_enable(True)
+    binding.profile_read(reset=True)
+    n0 = binding.launch_count()
+    clocks = Clocks(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for i in range(K):
+        dH, _, acc = step(q, pk[i], ek[i], uk[i])
+        dHs.append(dH)
+        accs.append(acc)
+    ev1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    launches = binding.launch_count() - n0
+    prof = binding.profile_read(reset=True)
+    binding.profile_enable(False)
+    ms_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t)
+    traj_per_s = world * B * K / (ms_max / 1e3)
+    acc_rate = float(np.mean(np.concatenate(accs)))
+
+    # end to end through the public API with host buffers: per step the
+    # momenta and noise go host -> device, Delta H and the decisions come back
+    ph = pk[:K].cpu().pin_memory()
+    eh = ek[:K].cpu().pin_memory()
+    pd = torch.empty_like(pk[0])
+    ed = torch.empty_like(ek[0])
+    q = q_start.clone()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(K):
+        pd.copy_(ph[i], non_blocking=True)
+        ed.copy_(eh[i], non_blocking=True)
+        step(q, pd, ed, uk[i])
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t)
+    h2d = int(pd.numel() * 8 + ed.numel() * 16 + B * 8)
+    d2h = int(B * (8 + 8 + 4))
+
+    # FP64 path on the same inputs: Delta H deviation and throughput
+    fp64 = None
+    if args.fp64_steps > 0:
+        md64 = P.MD(scheme=W["scheme"], tau=W["tau"], n=W["n"], M=W["M"], fg=W["fg"],
+                    cg=P.CG(tol=W["cg_tol"], maxit=20000, prec="f64"))
+        q64 = q_start.clone()
+        qm = q_start.clone()
+        dev_max = 0.0
+        acc64 = []
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        t64 = 0.0
+        for i in range(args.fp64_steps):
+            flush.fill_(1)
+            f0.record()
+            d64, _, a64 = lat.hmc_trajectory(q64, pk[i], ek[i], uk[i], md64, check=False)
+            f1.record()
+            torch.cuda.synchronize()
+            t64 += f0.elapsed_time(f1)
+            dm, _, _ = lat.hmc_trajectory(qm, pk[i], ek[i], uk[i], md, check=False)
+            ok = np.isfinite(d64) & np.isfinite(dm)
+            dev_max = max(dev_max, float(np.abs(d64[ok] - dm[ok]).max()) if ok.any() else 0.0)
+            acc64.append(a64)
+            qm.copy_(q64)
+        fp64 = {"traj_per_s": world * B * args.fp64_steps / (t64 / 1e3),
+                "acc": float(np.mean(np.concatenate(acc64))),
+                "max_abs_dH_mixed_minus_fp64": dev_max, "steps": args.fp64_steps}
+
+    # roofline of the dominant kernels (the CG iteration pair)
+    peaks, src = measured_peaks()
+    bps = CG_BYTES_PER_SITE_ITER[args.prec]
+    achieved = bps * prof["site_iters"] / (prof["iter_ms"] / 1e3) / 1e9 if prof["iter_ms"] else 0
+    peak = float(peaks["hbm_gbs"])
+    roofline = {"bound": "hbm", "kernel": "cg iteration (k_cg_a + k_cg_b)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": src,
+                "traffic": None,
+                "bytes_per_site_iter": bps, "site_iters": prof["site_iters"],
+                "kernel_ms": round(prof["iter_ms"], 3),
+                "kernel_share_of_step": round(prof["iter_ms"] / ms, 4),
+                "res_ms": round(prof["res_ms"], 3)}
+
+    if rank != 0:
+        return
+    cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu) else None
+    out = {
+        "metric": "HMC trajectories/s", "value": round(traj_per_s, 3),
+        "unit": "trajectories/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": round(ms_max / K, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.prec == "mixed" else "f64",
+        "data": "synthetic (own thermalised start, seeded momenta/noise)",
+        "config": dict(W, chains_per_gpu=B, precision=args.prec, parallelism=f"replicas{world}",
+                       l2="flushed between steps (256 MiB write)"),
+        "acceptance": round(acc_rate, 4),
+        "e2e": {"value": round(world * B * K / (e2e_ms / 1e3), 3), "unit": "trajectories/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "fp64": fp64,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------- oracle (CPU) ------
+
+def oracle_sample(seed=0):
+    """One trajectory of one chain of the workload with the FP64 oracle;
+    returns seconds."""
+    from oracle import integrators as ig
+    from oracle import schwinger as sw
+    from paper_1512_03812_gb300 import inputs as I
+    W = WORKLOAD
+    L, T = W["L"], W["T"]
+    lat = sw.Lattice(L, T, W["beta"], kappa_to_m0(W["kappa"]))
+    q = np.zeros((T, L, 2))
+    p = I.momenta(L, T, seed).reshape(T, L, 2)
+    eta = I.noise(L, T, seed + 1).reshape(T, L, 2)
+    t0 = time.time()
+    ig.hmc_trajectory(lat, q, p, eta, 0.5, W["scheme"], W["tau"], W["n"], M=W["M"], fg=W["fg"],
+                      solver=sw.Solver(tol=W["cg_tol"]))
+    return time.time() - t0
+
+
+def cpu_baseline(args):
+    dt = oracle_sample()
+    return {"value": round(1.0 / dt, 5), "unit": "trajectories/s", "cores": 1, "kind": "oracle",
+            "sample": "1 trajectory of 1 chain (64x64, cold start, same scheme and CG tolerance), "
+                      f"numpy FP64 single thread, {dt:.1f}s"}
+
+
+def run_reference(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(seed=100)
+    ts = [oracle_sample(seed=200 + i) for i in range(args.steps)]
+    v = len(ts) / sum(ts)
+    print(json.dumps({
+        "impl": "reference", "metric": "HMC trajectories/s", "value": round(v, 5),
+        "unit": "trajectories/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * sum(ts) / len(ts), 1), "higher_is_better": True,
+        "config": WORKLOAD, "dtype": "f64", "data": "synthetic",
+        "cpu_baseline": {"value": round(v, 5), "kind": "oracle", "cores": 1,
+                         "sample": "per step 1 trajectory of 1 chain, numpy FP64 single thread"},
+        "e2e": {"value": round(v, 5), "unit": "trajectories/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chains", type=int, default=WORKLOAD["chains_per_gpu"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "f64"])
+    ap.add_argument("--therm", type=int, default=20)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

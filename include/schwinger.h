@@ -1,0 +1,287 @@
+/*
+ * schwinger.h -- C ABI of the GB300 (sm_103a) Schwinger-model HMC library.
+ *
+ * The library implements the molecular-dynamics hot path of Hybrid Monte
+ * Carlo for the two-dimensional U(1) gauge theory with two degenerate Wilson
+ * fermions (one pseudofermion), as set out in "Adapted nested force-gradient
+ * integrators: the Schwinger model case" (arXiv:1512.03812):
+ *   the Wilson-Dirac operator D and D^dag (Sec. 3, Wilson-Dirac matrix),
+ *   conjugate-gradient solves of D^dag D x = phi (Sec. 3, Eq. fer_action,
+ *   Eq. chi_xi_vectors), the gauge and fermion forces (Eq. force_gauge,
+ *   Eq. force_fermion), the exact force-gradient term (Eq. force_gradient,
+ *   Eq. CFF, Eq. Z12) and its shifted-force approximation (Sec. 2), the
+ *   link and momentum updates (Sec. 2.1) and the integration schemes of
+ *   Sec. 2 (Eq. leap ... Eq. ad_5stage_multi_fg), and the HMC trajectory
+ *   with its Metropolis step (Sec. 2.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Batch.  A lattice object holds a batch of independent chains; chain c is an
+ *   L_c x T_c lattice with its own beta_c and m0_c.  Chains may differ in size.
+ *   Sites of all chains are stored back to back: chain c occupies global
+ *   sites [off_c, off_c + L_c T_c), off_0 = 0, off_{c+1} = off_c + L_c T_c.
+ *   Within a chain, site n = (x, t) has local index x + L_c t (x fastest).
+ * Directions.  mu = 0 is x (the paper's mu = 1), mu = 1 is t (mu = 2).
+ * Boundary conditions.  Gauge links are periodic; fermions are periodic in x
+ *   and antiperiodic in t.
+ * Layouts (all device memory, all owned by the caller):
+ *   link angles q, momenta p, forces F, C, directions v:
+ *       double [N][2]    (site-major, mu fastest), N = total sites
+ *   links U64: double [N][2][2]  -- U_mu(n) as (Re, Im); the antiperiodic
+ *       fermion sign is folded in: links U_t(x, T_c - 1) are stored negated.
+ *   links U32: float  [N][2][2]  -- the same in FP32.
+ *   spinors:  double [N][2][2] (FP64) or float [N][2][2] (FP32):
+ *       per site two spin components, each (Re, Im).
+ *   per-chain outputs (actions, Delta H, ...): double [nchains].
+ *   Every pointer must be aligned to 16 bytes.
+ * Streams.  `stream` is a cudaStream_t passed as void*; NULL is the legacy
+ *   default stream.  Entry points enqueue work on it and return without
+ *   synchronising, except where they return host-side results (marked
+ *   "synchronises").
+ * Workspace.  Entry points that need scratch take a device buffer `ws` of at
+ *   least sm_workspace_bytes(lat) bytes (256-byte aligned) and allocate
+ *   nothing themselves.  The contents of `ws` are not preserved between
+ *   calls, and two calls that use one workspace must not overlap in time.
+ * Errors.  Every entry point returns SM_OK (0) or an SM_ERR_* code and never
+ *   throws.  sm_last_error() returns the calling thread's last message.
+ *   After SM_ERR_CUDA the CUDA context may be unusable.
+ */
+#ifndef SCHWINGER_GB300_H
+#define SCHWINGER_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SM_OK 0
+#define SM_ERR_ARG 1            /* invalid argument (null, size, alignment) */
+#define SM_ERR_CUDA 2           /* a CUDA call failed */
+#define SM_ERR_NOT_CONVERGED 3  /* CG reached maxit for at least one chain */
+#define SM_ERR_TIMEOUT 4        /* a bounded device-side wait expired */
+#define SM_ERR_NAN 5            /* a non-finite value (e.g. Delta H) */
+
+/* arithmetic of a field or a solve */
+#define SM_F64 0    /* FP64 fields and FP64 CG */
+#define SM_F32 1    /* FP32 fields (apply_D / apply_DdagD only) */
+#define SM_MIXED 2  /* CG with FP32 iterations and FP64 reliable updates */
+
+/* which part of the action S = S_G + S_F (Eq. schwinger) */
+#define SM_PART_GAUGE 1
+#define SM_PART_FERMION 2
+#define SM_PART_FULL 3
+
+/* integration schemes of Sec. 2 */
+#define SM_LEAPFROG 0            /* Eq. leap */
+#define SM_FIVE_STAGE 1          /* Eq. 5stage (weight lambda; 1/6 as printed) */
+#define SM_FIVE_STAGE_FG 2       /* Eq. 5stage_fg, full C */
+#define SM_NESTED_LEAPFROG 3     /* Eq. leap_multi */
+#define SM_NESTED_FIVE_STAGE 4   /* Eq. 5stage_multi */
+#define SM_NESTED_FG 5           /* Eq. 5stage_multi_fg (C_FF outside, C_GG inside) */
+#define SM_ADAPTED_NESTED_FG 6   /* Eq. ad_5stage_multi_fg (C_FF outside, leapfrog inside) */
+
+/* how a force-gradient kick obtains C */
+#define SM_FG_EXACT 0    /* exact C via one extra CG (Eq. CFF, Eq. Z12) */
+#define SM_FG_SHIFTED 1  /* force at the shifted field q - (h^2/24) F(q) (Sec. 2) */
+
+typedef struct sm_lattice sm_lattice;
+
+/* CG parameters.  The solve of D^dag D x = b starts from x = 0 and stops, per
+ * chain, when |b - D^dag D x| <= tol |b|: for SM_F64 the recursive residual
+ * is tested, for SM_MIXED the FP64 true residual recomputed at each reliable
+ * update.  A reliable update is taken when the FP32 residual has fallen by
+ * the factor `delta` (0 < delta < 1) since the last one.  maxit bounds the
+ * iterations of every chain. */
+typedef struct {
+  double tol;
+  int maxit;
+  int prec;      /* SM_F64 or SM_MIXED */
+  double delta;  /* reliable-update factor, e.g. 0.1 (SM_MIXED only) */
+} sm_cg_params;
+
+/* One molecular-dynamics trajectory: n steps of size h = tau / n of `scheme`;
+ * M inner steps per inner block for the nested schemes; `lambda` the outer
+ * weight of the five-stage schemes (1/6 in Eq. 5stage; 0.1931833275 for
+ * Omelyan's minimum-norm variant); `fg` one of SM_FG_*.  With merge_kicks != 0
+ * adjacent kicks of the same action part are applied as one kick (the same
+ * flow, fewer force evaluations). */
+typedef struct {
+  int scheme;
+  double tau;
+  int n;
+  int M;
+  double lambda;
+  int fg;
+  int merge_kicks;
+  sm_cg_params cg;
+} sm_md_params;
+
+/* Counters accumulated over one call (zeroed by the call). */
+typedef struct {
+  long long cg_solves;         /* batched CG solves of D^dag D */
+  long long cg_iterations;     /* batched iterations (all chains advance together) */
+  long long chain_iterations;  /* sum over chains of their own iteration counts */
+  long long reliable_updates;  /* batched FP64 reliable-update passes */
+  long long inversions;        /* inversions of D in the paper's units (Sec. 3, end) */
+  long long force_evals;       /* fermion-force evaluations */
+  long long kernel_launches;   /* device kernels launched by this call */
+} sm_stats;
+
+/* ------------------------------------------------------------ library ---- */
+
+/* Thread-local description of the last error (never NULL). */
+const char* sm_last_error(void);
+/* ABI version: 1. */
+int sm_version(void);
+/* Total device kernels launched by this library in this process. */
+long long sm_launch_count(void);
+
+/* Kernel timing of the CG iterations, for roofline reporting.  While enabled,
+ * every chunk of batched CG iterations (the two kernels of an iteration,
+ * repeated) and every FP64 residual pass is bracketed by CUDA events on the
+ * solve's stream.  sm_profile_read returns the accumulated device time of the
+ * iteration kernels (iter_ms) and of the FP64 residual passes (res_ms), the
+ * number of batched iterations launched, and the number of site-iterations
+ * that did work (sum over chains of iterations x sites); reset != 0 zeroes
+ * the accumulators.  Not thread-safe; for one device. */
+int sm_profile_enable(int on);
+int sm_profile_read(double* iter_ms, double* res_ms, long long* batched_iters,
+                    long long* site_iters, int reset);
+
+/* ----------------------------------------------------- lattice objects ---- */
+
+/* Creates a batch of `nchains` >= 1 chains with sides L[c], T[c] >= 2 and
+ * couplings beta[c] (Eq. gauge_action) and m0[c] (bare mass of the
+ * Wilson-Dirac operator; kappa = 1 / (2 (2 + m0))).  Host arrays, copied.
+ * Allocates the geometry tables on the current device.  Returns
+ * SM_ERR_ARG on a bad size and SM_ERR_CUDA on an allocation failure. */
+int sm_lattice_create(int nchains, const int* L, const int* T, const double* beta,
+                      const double* m0, sm_lattice** out);
+int sm_lattice_destroy(sm_lattice* lat);
+/* Total number of sites N of the batch. */
+long long sm_lattice_sites(const sm_lattice* lat);
+int sm_lattice_chains(const sm_lattice* lat);
+/* Bytes of workspace the entry points below require for this lattice. */
+size_t sm_workspace_bytes(const sm_lattice* lat);
+
+/* ------------------------------------------------------- field set-up ---- */
+
+/* U_mu(n) = exp(i q_mu(n)) (Sec. 3, after Eq. gauge_action), with the
+ * antiperiodic fermion sign folded into the t-links on the last time slice.
+ * Writes U64 (may be NULL) and U32 (may be NULL). */
+int sm_links(const sm_lattice* lat, const double* q, double* U64, float* U32, void* stream);
+
+/* --------------------------------------------------- Wilson-Dirac D ------- */
+
+/* out = D in (dagger = 0) or D^dag in (dagger = 1), the Wilson-Dirac
+ * operator of Sec. 3:
+ *   (D psi)(n) = (2 + m0) psi(n) - 1/2 sum_mu [ (1 - sigma_mu) U_mu(n) psi(n+mu)
+ *                                  + (1 + sigma_mu) U_mu^dag(n-mu) psi(n-mu) ].
+ * prec = SM_F64: U, in, out are FP64 (U = U64); SM_F32: all FP32 (U = U32).
+ * `in` and `out` must not overlap. */
+int sm_apply_D(const sm_lattice* lat, const void* U, const void* in, void* out, int dagger,
+               int prec, void* stream);
+
+/* out = D^dag D in (Eq. fer_action), same conventions as sm_apply_D. */
+int sm_apply_DdagD(const sm_lattice* lat, const void* U, const void* in, void* out, int prec,
+                   void* ws, size_t ws_bytes, void* stream);
+
+/* -------------------------------------------------------- inversion ------- */
+
+/* Solves D^dag D x = b for every chain (Sec. 3: the inversions behind
+ * Eq. chi_xi_vectors; the solver is CG, see sm_cg_params).  U64 is always
+ * needed; U32 is needed for SM_MIXED and may be NULL for SM_F64.  b, x FP64
+ * spinors.  iters and relres (host arrays [nchains], may be NULL) receive
+ * each chain's iteration count and final FP64 true relative residual.
+ * Synchronises.  Returns SM_ERR_NOT_CONVERGED if a chain reached maxit
+ * (x then holds its last iterate). */
+int sm_cg_solve(const sm_lattice* lat, const double* U64, const float* U32, const double* b,
+                double* x, const sm_cg_params* cg, void* ws, size_t ws_bytes, int* iters,
+                double* relres, void* stream);
+
+/* ----------------------------------------------------------- forces ------- */
+
+/* F = dS_G/dq = beta g (Eq. force_gauge): F(n,x) = beta [sin th(n) - sin th(n-t)],
+ * F(n,t) = beta [sin th(n-x) - sin th(n)], th(n) the plaquette angle. */
+int sm_gauge_force(const sm_lattice* lat, const double* q, double* F, void* stream);
+
+/* F = dS_F/dq = f (Eq. force_fermion) with chi, xi of Eq. chi_xi_vectors for
+ * the pseudofermion phi (FP64 spinor).  One CG solve.  Synchronises. */
+int sm_fermion_force(const sm_lattice* lat, const double* q, const double* phi,
+                     const sm_cg_params* cg, double* F, void* ws, size_t ws_bytes,
+                     sm_stats* stats, void* stream);
+
+/* F = dS/dq for `part` (Eq. force).  Synchronises if part includes fermions. */
+int sm_force(const sm_lattice* lat, const double* q, const double* phi, int part,
+             const sm_cg_params* cg, double* F, void* ws, size_t ws_bytes, sm_stats* stats,
+             void* stream);
+
+/* F~ = F(q - (h^2/24) F(q)) for `part`: the shifted-field force whose Taylor
+ * expansion F - (h^2/48) C supplies the force-gradient kick without C
+ * (Sec. 2, the approximation after Eq. 5stage_fg).  Synchronises. */
+int sm_fg_shifted_force(const sm_lattice* lat, const double* q, const double* phi, int part,
+                        double h, const sm_cg_params* cg, double* F, void* ws,
+                        size_t ws_bytes, sm_stats* stats, void* stream);
+
+/* The exact force-gradient term C (Eq. force_gradient) for `part`:
+ * SM_PART_GAUGE -> C_GG, SM_PART_FERMION -> C_FF, SM_PART_FULL ->
+ * C_GG + C_FG + C_GF + C_FF (Eq. force_grad_de).  The fermion parts use the
+ * sum-before-invert vectors Z_1, Z_2 of Eq. Z12, obtained from one CG solve.
+ * F (may be NULL) receives the force of the same part.  Synchronises. */
+int sm_force_gradient(const sm_lattice* lat, const double* q, const double* phi, int part,
+                      const sm_cg_params* cg, double* C, double* F, void* ws,
+                      size_t ws_bytes, sm_stats* stats, void* stream);
+
+/* Hessian-vector product Hv = (d^2 S / dq dq) v for `part`: the second
+ * derivative of Sec. 3.1 contracted with an arbitrary link field v (Eq. CFF
+ * and Eq. Z12 with f replaced by v give 2 Hv for the fermion part).
+ * Two CG solves for the fermion part.  Synchronises. */
+int sm_hvp(const sm_lattice* lat, const double* q, const double* phi, int part,
+           const double* v, const sm_cg_params* cg, double* Hv, void* ws, size_t ws_bytes,
+           sm_stats* stats, void* stream);
+
+/* Per-chain actions (device arrays [nchains]; each may be NULL):
+ * S_G = beta sum (1 - Re P) (Eq. gauge_action), S_F = phi^dag (D^dag D)^{-1} phi
+ * (Eq. fer_action; phi may be NULL when S_F is NULL) and the kinetic term
+ * 1/2 sum p^2 (Eq. schwinger; p may be NULL when K is NULL).  FP64 sums in a
+ * fixed order.  Synchronises if S_F is requested. */
+int sm_energies(const sm_lattice* lat, const double* q, const double* p, const double* phi,
+                const sm_cg_params* cg, double* K, double* S_G, double* S_F, void* ws,
+                size_t ws_bytes, sm_stats* stats, void* stream);
+
+/* --------------------------------------------------- integration ---------- */
+
+/* Runs one MD trajectory (md->n steps of md->scheme, Sec. 2) in place on the
+ * links q and momenta p of every chain, with pseudofermion phi.
+ * Synchronises. */
+int sm_md_trajectory(const sm_lattice* lat, double* q, double* p, const double* phi,
+                     const sm_md_params* md, void* ws, size_t ws_bytes, sm_stats* stats,
+                     void* stream);
+
+/* One step of size h of md->scheme (md->tau and md->n are ignored). */
+int sm_md_step(const sm_lattice* lat, double* q, double* p, const double* phi,
+               const sm_md_params* md, double h, void* ws, size_t ws_bytes, sm_stats* stats,
+               void* stream);
+
+/* One HMC update of every chain (Sec. 2.1).  Inputs: links q (device, in/out),
+ * momenta p0 and Gaussian noise eta (device, read only), Metropolis uniforms
+ * u[nchains] in [0, 1) (host).  The pseudofermion is phi = D^dag eta at the
+ * starting links; H = 1/2 sum p^2 + S_G + S_F (Eq. schwinger) is summed in FP64
+ * before and after the trajectory; chain c is accepted iff
+ * Delta H_c <= 0 or u[c] < exp(-Delta H_c), and a rejected (or non-finite)
+ * chain gets its starting links back.  dH and H0 (host [nchains], H0 may be
+ * NULL) receive Delta H and H at the start, accepted (host [nchains]) 1 or 0.
+ * If p_out (device, may be NULL) is given it receives the momenta at the end
+ * of the trajectory and q_md (device, may be NULL) the links before the
+ * Metropolis step.  Synchronises. */
+int sm_hmc_trajectory(const sm_lattice* lat, double* q, const double* p0, const double* eta,
+                      const double* u, const sm_md_params* md, void* ws, size_t ws_bytes,
+                      double* dH, double* H0, int* accepted, double* p_out, double* q_md,
+                      sm_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCHWINGER_GB300_H */

@@ -1,0 +1,475 @@
+// md.cu -- forces, force-gradient terms, energies, the integration schemes of
+// Sec. 2 and the HMC trajectory, as host-side sequences of the site kernels
+// (core.cu) and CG solves (solver.cu).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sm {
+
+#define SM_CU(call)                                                                           \
+  do {                                                                                        \
+    const cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) return fail(SM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+#define SM_TRY(expr)            \
+  do {                          \
+    const int rc_ = (expr);     \
+    if (rc_ != SM_OK) return rc_; \
+  } while (0)
+
+static bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+static int check_cg(const sm_cg_params* cg) {
+  if (!cg) return fail(SM_ERR_ARG, "cg params are NULL");
+  if (cg->prec != SM_F64 && cg->prec != SM_MIXED)
+    return fail(SM_ERR_ARG, "cg prec must be SM_F64 or SM_MIXED");
+  return SM_OK;
+}
+
+static int check_part(int part) {
+  if (part < SM_PART_GAUGE || part > SM_PART_FULL) return fail(SM_ERR_ARG, "bad part %d", part);
+  return SM_OK;
+}
+
+// U64 (and U32 for mixed solves) from q.
+static int make_links(Ctx& c, const double* q, double* U64, float* U32, const sm_cg_params& cg) {
+  return launch_links(c, q, U64, cg.prec == SM_MIXED ? U32 : nullptr);
+}
+
+// xi = (D^dag D)^{-1} phi and chi = D xi (Eq. chi_xi_vectors), in c.w.xi, c.w.chi.
+static int chi_xi(Ctx& c, const double* U64, const float* U32, const double* phi,
+                  const sm_cg_params& cg) {
+  SM_TRY(cg_solve(c, U64, U32, phi, c.w.xi, cg, nullptr, nullptr));
+  c.st->inversions += 2;
+  c.st->force_evals++;
+  return launch_dslash<double>(c, U64, c.w.xi, c.w.chi, false, nullptr, 0.0);
+}
+
+// The force of `part` at q (links U64/U32 of q): written to F (if not NULL)
+// and/or applied as the kick p -= eps F (if p is not NULL).
+static int force_at(Ctx& c, const double* q, const double* U64, const float* U32,
+                    const double* phi, int part, const sm_cg_params& cg, double* F, double* p,
+                    double eps) {
+  if (part & SM_PART_GAUGE) SM_TRY(launch_gauge_kick(c, q, p, eps, F, false));
+  if (part & SM_PART_FERMION) {
+    SM_TRY(chi_xi(c, U64, U32, phi, cg));
+    SM_TRY(launch_fermion_kick(c, U64, c.w.chi, c.w.xi, p, eps, F, (part & SM_PART_GAUGE) != 0));
+  }
+  return SM_OK;
+}
+
+// C = 2 (Hess S_part) v at q.  For the fermion part chi and xi of q must be in
+// c.w.chi and c.w.xi.  The sums over (m, nu) of Eq. Z12 are formed before the
+// single inversion:  D^dag D Z2 = D^dag s2 + s1,  Z1 = D Z2 - s2.
+static int hess_times(Ctx& c, const double* q, const double* U64, const float* U32, int part,
+                      const double* v, const sm_cg_params& cg, double* C) {
+  bool acc = false;
+  if (part & SM_PART_GAUGE) {
+    SM_TRY(launch_gauge_hvp(c, q, v, C, false));
+    acc = true;
+  }
+  if (part & SM_PART_FERMION) {
+    SM_TRY(launch_deriv_hop(c, U64, v, c.w.chi, c.w.s1, true));   // sum w_1 v
+    SM_TRY(launch_deriv_hop(c, U64, v, c.w.xi, c.w.s2, false));   // sum w_2 v
+    SM_TRY(launch_dslash<double>(c, U64, c.w.s2, c.w.b, true, c.w.s1, 1.0));
+    SM_TRY(cg_solve(c, U64, U32, c.w.b, c.w.z2, cg, nullptr, nullptr));
+    c.st->inversions += 2;
+    SM_TRY(launch_dslash<double>(c, U64, c.w.z2, c.w.z1, false, c.w.s2, -1.0));
+    SM_TRY(launch_fg_assemble(c, U64, c.w.chi, c.w.xi, c.w.z1, c.w.z2, v, C, acc));
+  }
+  return SM_OK;
+}
+
+// F of `part` into c.w.F and C = 2 Hess F into C (Eq. force_gradient).
+static int force_and_gradient(Ctx& c, const double* q, const double* U64, const float* U32,
+                              const double* phi, int part, const sm_cg_params& cg, double* C) {
+  SM_TRY(force_at(c, q, U64, U32, phi, part, cg, c.w.F, nullptr, 0.0));
+  return hess_times(c, q, U64, U32, part, c.w.F, cg, C);
+}
+
+// F(q - (h^2/24) F(q)) of `part` into F and/or as the kick p -= eps F.
+static int shifted_force(Ctx& c, const double* q, const double* U64, const float* U32,
+                         const double* phi, int part, double h, const sm_cg_params& cg, double* F,
+                         double* p, double eps) {
+  SM_TRY(force_at(c, q, U64, U32, phi, part, cg, c.w.F, nullptr, 0.0));
+  SM_TRY(launch_lincomb(c, c.w.qs, q, -h * h / 24.0, c.w.F, 0.0, nullptr));
+  if (part & SM_PART_FERMION) SM_TRY(make_links(c, c.w.qs, c.w.U64s, c.w.U32s, cg));
+  return force_at(c, c.w.qs, c.w.U64s, c.w.U32s, phi, part, cg, F, p, eps);
+}
+
+// ------------------------------------------------------------- schedules --
+
+enum OpKind { OP_DRIFT, OP_KICK, OP_FG };
+struct Op {
+  OpKind k;
+  int part;
+  double eps;  // drift/kick step; for OP_FG the step h of the force-gradient stage
+};
+
+static void inner_lf(std::vector<Op>& o, double h, int M) {
+  for (int i = 0; i < M; ++i) {
+    o.push_back({OP_KICK, SM_PART_GAUGE, h / (2.0 * M)});
+    o.push_back({OP_DRIFT, 0, h / M});
+    o.push_back({OP_KICK, SM_PART_GAUGE, h / (2.0 * M)});
+  }
+}
+
+static void inner_fg(std::vector<Op>& o, double h, int M) {
+  const double hm = h / M;
+  for (int i = 0; i < M; ++i) {
+    o.push_back({OP_KICK, SM_PART_GAUGE, hm / 6.0});
+    o.push_back({OP_DRIFT, 0, hm / 2.0});
+    o.push_back({OP_FG, SM_PART_GAUGE, hm});
+    o.push_back({OP_DRIFT, 0, hm / 2.0});
+    o.push_back({OP_KICK, SM_PART_GAUGE, hm / 6.0});
+  }
+}
+
+// The operations of one step of size h, written as the compositions of
+// Sec. 2 (Eq. leap, 5stage, 5stage_fg, leap_multi, 5stage_multi,
+// 5stage_multi_fg, ad_5stage_multi_fg).
+static int build_step(std::vector<Op>& o, const sm_md_params& md, double h) {
+  const int F = SM_PART_FULL, Fe = SM_PART_FERMION;
+  const double lam = md.lambda;
+  const int M = md.M;
+  switch (md.scheme) {
+    case SM_LEAPFROG:
+      o.push_back({OP_KICK, F, h / 2});
+      o.push_back({OP_DRIFT, 0, h});
+      o.push_back({OP_KICK, F, h / 2});
+      return SM_OK;
+    case SM_FIVE_STAGE:
+      o.push_back({OP_KICK, F, lam * h});
+      o.push_back({OP_DRIFT, 0, h / 2});
+      o.push_back({OP_KICK, F, (1 - 2 * lam) * h});
+      o.push_back({OP_DRIFT, 0, h / 2});
+      o.push_back({OP_KICK, F, lam * h});
+      return SM_OK;
+    case SM_FIVE_STAGE_FG:
+      o.push_back({OP_KICK, F, h / 6});
+      o.push_back({OP_DRIFT, 0, h / 2});
+      o.push_back({OP_FG, F, h});
+      o.push_back({OP_DRIFT, 0, h / 2});
+      o.push_back({OP_KICK, F, h / 6});
+      return SM_OK;
+    case SM_NESTED_LEAPFROG:
+      o.push_back({OP_KICK, Fe, h / 2});
+      inner_lf(o, h, M);
+      o.push_back({OP_KICK, Fe, h / 2});
+      return SM_OK;
+    case SM_NESTED_FIVE_STAGE:
+      o.push_back({OP_KICK, Fe, lam * h});
+      inner_lf(o, h / 2, M);
+      o.push_back({OP_KICK, Fe, (1 - 2 * lam) * h});
+      inner_lf(o, h / 2, M);
+      o.push_back({OP_KICK, Fe, lam * h});
+      return SM_OK;
+    case SM_NESTED_FG:
+      o.push_back({OP_KICK, Fe, h / 6});
+      inner_fg(o, h / 2, M);
+      o.push_back({OP_FG, Fe, h});
+      inner_fg(o, h / 2, M);
+      o.push_back({OP_KICK, Fe, h / 6});
+      return SM_OK;
+    case SM_ADAPTED_NESTED_FG:
+      o.push_back({OP_KICK, Fe, h / 6});
+      inner_lf(o, h / 2, M);
+      o.push_back({OP_FG, Fe, h});
+      inner_lf(o, h / 2, M);
+      o.push_back({OP_KICK, Fe, h / 6});
+      return SM_OK;
+    default:
+      return fail(SM_ERR_ARG, "unknown scheme %d", md.scheme);
+  }
+}
+
+// Adjacent kicks of the same part at the same links are one kick.
+static void merge(std::vector<Op>& o) {
+  std::vector<Op> m;
+  for (const Op& op : o) {
+    if (!m.empty() && op.k == OP_KICK && m.back().k == OP_KICK && m.back().part == op.part)
+      m.back().eps += op.eps;
+    else
+      m.push_back(op);
+  }
+  o.swap(m);
+}
+
+static int check_md(const sm_md_params* md) {
+  if (!md) return fail(SM_ERR_ARG, "md params are NULL");
+  if (md->scheme < SM_LEAPFROG || md->scheme > SM_ADAPTED_NESTED_FG)
+    return fail(SM_ERR_ARG, "unknown scheme %d", md->scheme);
+  if (md->M < 1) return fail(SM_ERR_ARG, "M = %d < 1", md->M);
+  if (md->fg != SM_FG_EXACT && md->fg != SM_FG_SHIFTED) return fail(SM_ERR_ARG, "bad fg mode");
+  return check_cg(&md->cg);
+}
+
+// Executes `ops` on (q, p).  Links are refreshed lazily, only before an
+// operation that needs the fermion force.
+static int execute(Ctx& c, const std::vector<Op>& ops, double* q, double* p, const double* phi,
+                   const sm_md_params& md) {
+  bool links_ok = false;
+  const sm_cg_params& cg = md.cg;
+  for (const Op& op : ops) {
+    if ((op.k != OP_DRIFT) && (op.part & SM_PART_FERMION) && !links_ok) {
+      SM_TRY(make_links(c, q, c.w.U64, c.w.U32, cg));
+      links_ok = true;
+    }
+    switch (op.k) {
+      case OP_DRIFT:
+        SM_TRY(launch_drift(c, q, p, op.eps));
+        links_ok = false;
+        break;
+      case OP_KICK:
+        SM_TRY(force_at(c, q, c.w.U64, c.w.U32, phi, op.part, cg, nullptr, p, op.eps));
+        break;
+      case OP_FG: {
+        // e^{(2/3) h B + (1/72) h^3 C}:  p <- p - (2h/3) F + (h^3/72) C
+        const double h = op.eps;
+        if (md.fg == SM_FG_EXACT) {
+          SM_TRY(force_and_gradient(c, q, c.w.U64, c.w.U32, phi, op.part, cg, c.w.C));
+          SM_TRY(launch_lincomb(c, p, p, -2.0 * h / 3.0, c.w.F, h * h * h / 72.0, c.w.C));
+        } else {
+          SM_TRY(shifted_force(c, q, c.w.U64, c.w.U32, phi, op.part, h, cg, nullptr, p,
+                               2.0 * h / 3.0));
+        }
+        break;
+      }
+    }
+  }
+  return SM_OK;
+}
+
+static int md_run(Ctx& c, double* q, double* p, const double* phi, const sm_md_params& md,
+                  double h, int nsteps) {
+  std::vector<Op> ops;
+  for (int i = 0; i < nsteps; ++i) SM_TRY(build_step(ops, md, h));
+  if (md.merge_kicks) merge(ops);
+  return execute(c, ops, q, p, phi, md);
+}
+
+}  // namespace sm
+
+// ============================================================== C ABI =====
+
+using namespace sm;
+
+// The error code for chains whose solves failed during a trajectory.
+static int chain_failures(const Ctx& c, const char* who) {
+  int nan = 0, nc = 0;
+  for (int f : c.chain_flags) {
+    nan += (f & 2) != 0;
+    nc += (f & 1) != 0;
+  }
+  if (nan) return fail(SM_ERR_NAN, "%s: %d chain(s) hit a non-finite value", who, nan);
+  if (nc) return fail(SM_ERR_NOT_CONVERGED, "%s: CG reached maxit on %d chain(s)", who, nc);
+  return SM_OK;
+}
+
+static int fields_ok(std::initializer_list<const void*> ps, const char* who) {
+  for (const void* p : ps) {
+    if (!p) return fail(SM_ERR_ARG, "%s: NULL field", who);
+    if (!al16(p)) return fail(SM_ERR_ARG, "%s: field not 16-byte aligned", who);
+  }
+  return SM_OK;
+}
+
+extern "C" {
+
+int sm_gauge_force(const sm_lattice* lat, const double* q, double* F, void* stream) {
+  Ctx c;
+  SM_TRY(c.init(lat, nullptr, 0, stream, nullptr));
+  SM_TRY(fields_ok({q, F}, "sm_gauge_force"));
+  return launch_gauge_kick(c, q, nullptr, 0.0, F, false);
+}
+
+int sm_force(const sm_lattice* lat, const double* q, const double* phi, int part,
+             const sm_cg_params* cg, double* F, void* ws, size_t ws_bytes, sm_stats* stats,
+             void* stream) {
+  Ctx c;
+  SM_TRY(c.init(lat, ws, ws_bytes, stream, stats));
+  SM_TRY(check_part(part));
+  SM_TRY(fields_ok({q, F}, "sm_force"));
+  if (part & SM_PART_FERMION) {
+    SM_TRY(check_cg(cg));
+    SM_TRY(fields_ok({phi}, "sm_force"));
+    SM_TRY(make_links(c, q, c.w.U64, c.w.U32, *cg));
+  }
+  sm_cg_params dummy{1e-10, 1, SM_F64, 0.1};
+  SM_TRY(force_at(c, q, c.w.U64, c.w.U32, phi, part, cg ? *cg : dummy, F, nullptr, 0.0));
+  return c.sync();
+}
+
+int sm_fermion_force(const sm_lattice* lat, const double* q, const double* phi,
+                     const sm_cg_params* cg, double* F, void* ws, size_t ws_bytes,
+                     sm_stats* stats, void* stream) {
+  return sm_force(lat, q, phi, SM_PART_FERMION, cg, F, ws, ws_bytes, stats, stream);
+}
+
+int sm_fg_shifted_force(const sm_lattice* lat, const double* q, const double* phi, int part,
+                        double h, const sm_cg_params* cg, double* F, void* ws, size_t ws_bytes,
+                        sm_stats* stats, void* stream) {
+  Ctx c;
+  SM_TRY(c.init(lat, ws, ws_bytes, stream, stats));
+  SM_TRY(check_part(part));
+  SM_TRY(check_cg(cg));
+  SM_TRY(fields_ok({q, F}, "sm_fg_shifted_force"));
+  if (part & SM_PART_FERMION) {
+    SM_TRY(fields_ok({phi}, "sm_fg_shifted_force"));
+    SM_TRY(make_links(c, q, c.w.U64, c.w.U32, *cg));
+  }
+  SM_TRY(shifted_force(c, q, c.w.U64, c.w.U32, phi, part, h, *cg, F, nullptr, 0.0));
+  return c.sync();
+}
+
+int sm_force_gradient(const sm_lattice* lat, const double* q, const double* phi, int part,
+                      const sm_cg_params* cg, double* C, double* F, void* ws, size_t ws_bytes,
+                      sm_stats* stats, void* stream) {
+  Ctx c;
+  SM_TRY(c.init(lat, ws, ws_bytes, stream, stats));
+  SM_TRY(check_part(part));
+  SM_TRY(check_cg(cg));
+  SM_TRY(fields_ok({q, C}, "sm_force_gradient"));
+  if (F && !al16(F)) return fail(SM_ERR_ARG, "sm_force_gradient: F not aligned");
+  if (part & SM_PART_FERMION) {
+    SM_TRY(fields_ok({phi}, "sm_force_gradient"));
+    SM_TRY(make_links(c, q, c.w.U64, c.w.U32, *cg));
+  }
+  SM_TRY(force_and_gradient(c, q, c.w.U64, c.w.U32, phi, part, *cg, C));
+  if (F) SM_CU(cudaMemcpyAsync(F, c.w.F, sizeof(double) * 2 * lat->N, cudaMemcpyDeviceToDevice, c.s));
+  return c.sync();
+}
+
+int sm_hvp(const sm_lattice* lat, const double* q, const double* phi, int part, const double* v,
+           const sm_cg_params* cg, double* Hv, void* ws, size_t ws_bytes, sm_stats* stats,
+           void* stream) {
+  Ctx c;
+  SM_TRY(c.init(lat, ws, ws_bytes, stream, stats));
+  SM_TRY(check_part(part));
+  SM_TRY(check_cg(cg));
+  SM_TRY(fields_ok({q, v, Hv}, "sm_hvp"));
+  if (part & SM_PART_FERMION) {
+    SM_TRY(fields_ok({phi}, "sm_hvp"));
+    SM_TRY(make_links(c, q, c.w.U64, c.w.U32, *cg));
+    SM_TRY(chi_xi(c, c.w.U64, c.w.U32, phi, *cg));
+  }
+  SM_TRY(launch_lincomb(c, c.w.v, nullptr, 1.0, v, 0.0, nullptr));
+  SM_TRY(hess_times(c, q, c.w.U64, c.w.U32, part, c.w.v, *cg, Hv));
+  SM_TRY(launch_lincomb(c, Hv, nullptr, 0.5, Hv, 0.0, nullptr));
+  return c.sync();
+}
+
+int sm_energies(const sm_lattice* lat, const double* q, const double* p, const double* phi,
+                const sm_cg_params* cg, double* K, double* S_G, double* S_F, void* ws,
+                size_t ws_bytes, sm_stats* stats, void* stream) {
+  Ctx c;
+  SM_TRY(c.init(lat, ws, ws_bytes, stream, stats));
+  if ((K && !p) || ((S_G || S_F) && !q)) return fail(SM_ERR_ARG, "sm_energies: missing field");
+  if (S_F) {
+    SM_TRY(check_cg(cg));
+    SM_TRY(fields_ok({q, phi}, "sm_energies"));
+    SM_TRY(make_links(c, q, c.w.U64, c.w.U32, *cg));
+    SM_TRY(cg_solve(c, c.w.U64, c.w.U32, phi, c.w.xi, *cg, nullptr, nullptr));
+  }
+  SM_TRY(launch_energies(c, S_G ? q : nullptr, K ? p : nullptr, S_F ? phi : nullptr,
+                         S_F ? c.w.xi : nullptr, K, S_G, S_F));
+  return c.sync();
+}
+
+int sm_md_trajectory(const sm_lattice* lat, double* q, double* p, const double* phi,
+                     const sm_md_params* md, void* ws, size_t ws_bytes, sm_stats* stats,
+                     void* stream) {
+  Ctx c;
+  SM_TRY(c.init(lat, ws, ws_bytes, stream, stats));
+  SM_TRY(check_md(md));
+  if (md->n < 1 || !(md->tau > 0)) return fail(SM_ERR_ARG, "md: n >= 1 and tau > 0 required");
+  SM_TRY(fields_ok({q, p, phi}, "sm_md_trajectory"));
+  c.strict = false;
+  SM_TRY(md_run(c, q, p, phi, *md, md->tau / md->n, md->n));
+  SM_TRY(c.sync());
+  return chain_failures(c, "sm_md_trajectory");
+}
+
+int sm_md_step(const sm_lattice* lat, double* q, double* p, const double* phi,
+               const sm_md_params* md, double h, void* ws, size_t ws_bytes, sm_stats* stats,
+               void* stream) {
+  Ctx c;
+  SM_TRY(c.init(lat, ws, ws_bytes, stream, stats));
+  SM_TRY(check_md(md));
+  SM_TRY(fields_ok({q, p, phi}, "sm_md_step"));
+  c.strict = false;
+  SM_TRY(md_run(c, q, p, phi, *md, h, 1));
+  SM_TRY(c.sync());
+  return chain_failures(c, "sm_md_step");
+}
+
+int sm_hmc_trajectory(const sm_lattice* lat, double* q, const double* p0, const double* eta,
+                      const double* u, const sm_md_params* md, void* ws, size_t ws_bytes,
+                      double* dH, double* H0, int* accepted, double* p_out, double* q_md,
+                      sm_stats* stats, void* stream) {
+  Ctx c;
+  SM_TRY(c.init(lat, ws, ws_bytes, stream, stats));
+  SM_TRY(check_md(md));
+  if (md->n < 1 || !(md->tau > 0)) return fail(SM_ERR_ARG, "md: n >= 1 and tau > 0 required");
+  SM_TRY(fields_ok({q, p0, eta}, "sm_hmc_trajectory"));
+  if (!u || !dH || !accepted) return fail(SM_ERR_ARG, "sm_hmc_trajectory: NULL host output");
+  if ((p_out && !al16(p_out)) || (q_md && !al16(q_md)))
+    return fail(SM_ERR_ARG, "sm_hmc_trajectory: unaligned output");
+  const int nc = lat->nchains;
+  const size_t lbytes = sizeof(double) * 2 * (size_t)lat->N;
+  const sm_cg_params& cg = md->cg;
+  double* out = c.w.out;  // [8][nc]: K0, SG0, SF0, K1, SG1, SF1
+  c.strict = false;       // a failing chain is rejected, the others go on
+
+  // heatbath phi = D^dag eta at the starting links; H at the start
+  SM_TRY(make_links(c, q, c.w.U64, c.w.U32, cg));
+  SM_TRY(launch_dslash<double>(c, c.w.U64, eta, c.w.phi, true, nullptr, 0.0));
+  SM_CU(cudaMemcpyAsync(c.w.qsave, q, lbytes, cudaMemcpyDeviceToDevice, c.s));
+  SM_CU(cudaMemcpyAsync(c.w.pw, p0, lbytes, cudaMemcpyDeviceToDevice, c.s));
+  SM_TRY(cg_solve(c, c.w.U64, c.w.U32, c.w.phi, c.w.xi, cg, nullptr, nullptr));
+  SM_TRY(launch_energies(c, q, c.w.pw, c.w.phi, c.w.xi, out, out + nc, out + 2 * nc));
+
+  // molecular dynamics
+  SM_TRY(md_run(c, q, c.w.pw, c.w.phi, *md, md->tau / md->n, md->n));
+
+  // H at the end
+  SM_TRY(make_links(c, q, c.w.U64, c.w.U32, cg));
+  SM_TRY(cg_solve(c, c.w.U64, c.w.U32, c.w.phi, c.w.xi, cg, nullptr, nullptr));
+  SM_TRY(launch_energies(c, q, c.w.pw, c.w.phi, c.w.xi, out + 3 * nc, out + 4 * nc, out + 5 * nc));
+  std::vector<double> h(6 * (size_t)nc);
+  SM_CU(cudaMemcpyAsync(h.data(), out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c.s));
+  SM_CU(cudaStreamSynchronize(c.s));
+
+  // Metropolis: accept iff dH <= 0 or u < exp(-dH); non-finite dH rejects
+  std::vector<int> reject(nc);
+  bool any_nan = false, any_reject = false;
+  for (int i = 0; i < nc; ++i) {
+    const double h0 = h[i] + h[nc + i] + h[2 * nc + i];
+    const double h1 = h[3 * nc + i] + h[4 * nc + i] + h[5 * nc + i];
+    const double d = h1 - h0;
+    dH[i] = d;
+    if (H0) H0[i] = h0;
+    const bool solved = c.chain_flags.empty() || c.chain_flags[i] == 0;
+    const bool ok = solved && std::isfinite(d) && (d <= 0.0 || u[i] < std::exp(-d));
+    accepted[i] = ok ? 1 : 0;
+    reject[i] = ok ? 0 : 1;
+    any_reject |= !ok;
+    any_nan |= !std::isfinite(d);
+  }
+  if (p_out) SM_CU(cudaMemcpyAsync(p_out, c.w.pw, lbytes, cudaMemcpyDeviceToDevice, c.s));
+  if (q_md) SM_CU(cudaMemcpyAsync(q_md, q, lbytes, cudaMemcpyDeviceToDevice, c.s));
+  if (any_reject) {
+    SM_CU(cudaMemcpyAsync(c.w.flags, reject.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, c.s));
+    SM_TRY(launch_copy_links_masked(c, q, c.w.qsave, c.w.flags));
+  }
+  SM_TRY(c.sync());
+  if (any_nan) return fail(SM_ERR_NAN, "sm_hmc_trajectory: non-finite Delta H (chain rejected)");
+  return chain_failures(c, "sm_hmc_trajectory");
+}
+
+}  // extern "C"

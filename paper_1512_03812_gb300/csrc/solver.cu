@@ -1,0 +1,494 @@
+// solver.cu -- batched conjugate gradient on D^dag D x = b.
+//
+// The paper does not name its solver for the inversions of D (Sec. 3, end);
+// CG on the normal operator is used.  All chains of the batch iterate in the
+// same launches; each chain carries its own scalars (CgChain) and leaves the
+// iteration when it converges: its blocks then exit at once.
+//
+// One iteration is two kernels:
+//   A: p <- r + beta p (recomputed at the four neighbours, so no extra pass),
+//      t <- D p, and |t|^2 = p^dag D^dag D p  ->  alpha = |r|^2 / |t|^2
+//   B: A p = D^dag t, x <- x + alpha p, r <- r - alpha A p, |r|^2 -> beta
+// Two search-direction buffers alternate; each chain records which one holds
+// its p, so kernel arguments never change between iterations.
+//
+// SM_F64: FP64 fields; the chain stops when |r| <= tol |b| for the recursive
+// residual, and the FP64 true residual is reported at the end.
+// SM_MIXED: FP32 fields for x, r, p, t and FP32 links; reliable updates
+// (Sleijpen and van der Vorst; in the mixed-precision form of Clark et al.,
+// 2010) fold the FP32 solution into the FP64 x and replace r by the FP64 true
+// residual b - A x whenever |r| has fallen by `delta` since the last update,
+// and when the FP32 residual meets the tolerance.  The chain stops when the
+// FP64 true residual meets it.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sm {
+
+#define SM_CU(call)                                                                           \
+  do {                                                                                        \
+    const cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) return fail(SM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename R>
+struct CgArgs {
+  const R* U;        // links in the iteration precision
+  const double* U64; // FP64 links (reliable updates, true residual)
+  const double* b;
+  R* r;
+  R* x;              // iterate: the solution (F64) or its FP32 correction (MIXED)
+  R* pa;
+  R* pb;
+  R* t;
+  double* xhi;       // FP64 solution (MIXED)
+  double* t64;       // FP64 scratch (reliable updates)
+  CgChain* cgc;
+  double* partials;
+  unsigned* counters;
+  int* n_active;
+  double tol2, delta2;
+  int maxit;
+  int mixed;
+};
+
+#define CHAIN_PROLOGUE                     \
+  const int c_ = g.blk_chain[blockIdx.x];  \
+  const ChainInfo ci = g.chains[c_];       \
+  CgChain* cc = a.cgc + c_;
+
+template <typename R>
+__device__ __forceinline__ Sp<R> to_r(Sp<double> v) {
+  return {{(R)v.a.re, (R)v.a.im}, {(R)v.b.re, (R)v.b.im}};
+}
+__device__ __forceinline__ Sp<double> to_d(Sp<float> v) {
+  return {{v.a.re, v.a.im}, {v.b.re, v.b.im}};
+}
+__device__ __forceinline__ Sp<double> to_d(Sp<double> v) { return v; }
+
+// r = b, x = 0, p = 0, |b|^2 -> the chain's scalars.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_cg_init(Geo g, CgArgs<R> a) {
+  CHAIN_PROLOGUE
+  const Site s = site_of(g, ci, c_);
+  double v[1] = {0.0};
+  if (s.valid) {
+    const Sp<double> bv = ld_sp(a.b, s.n);
+    v[0] = norm2(bv);
+    const Sp<R> z = {{0, 0}, {0, 0}};
+    st_sp(a.r, s.n, to_r<R>(bv));
+    st_sp(a.x, s.n, z);
+    st_sp(a.pa, s.n, z);
+    if (a.mixed) st_sp(a.xhi, s.n, Sp<double>{{0, 0}, {0, 0}});
+  }
+  double tot[1];
+  if (chain_reduce<1>(v, a.partials, a.counters, g, ci, c_, tot) && threadIdx.x == 0) {
+    const double bb = tot[0];
+    cc->bb = bb;
+    cc->rr = cc->rr_prev = cc->rmax = cc->rr_true = bb;
+    cc->alpha = cc->beta = 0.0;
+    cc->iters = 0;
+    cc->par = 0;
+    cc->need_update = 0;
+    cc->flags = 0;
+    if (bb > 0.0 && isfinite(bb)) {
+      cc->state = 1;
+      atomicAdd(a.n_active, 1);
+    } else {
+      cc->state = 0;
+      if (!isfinite(bb)) cc->flags |= 2;
+    }
+  }
+}
+
+// Kernel A: p <- r + beta p at n and its neighbours; t = D p; alpha.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_cg_a(Geo g, CgArgs<R> a) {
+  CHAIN_PROLOGUE
+  if (cc->state != 1) return;
+  const Site s = site_of(g, ci, c_);
+  const int par = cc->par;
+  const R beta = (R)cc->beta;
+  const R* __restrict__ pold = par ? a.pb : a.pa;
+  R* __restrict__ pnew = par ? a.pa : a.pb;
+  double v[1] = {0.0};
+  if (s.valid) {
+    auto P = [&](long long m) { return ld_sp(a.r, m) + beta * ld_sp(pold, m); };
+    const long long nxm = at(s, xm1(s), s.t), ntm = at(s, s.x, tm1(s));
+    const Sp<R> p0 = P(s.n);
+    st_sp(pnew, s.n, p0);
+    const Lk<R> u = ld_lk(a.U, s.n);
+    const Sp<R> o = hop_sum<false, R>(P(at(s, xp1(s), s.t)), P(nxm), P(at(s, s.x, tp1(s))), P(ntm),
+                                      u.x, ld_lk(a.U, nxm).x, u.t, ld_lk(a.U, ntm).t);
+    const Sp<R> tv = (R)(2.0 + ci.m0) * p0 - (R)0.5 * o;
+    st_sp(a.t, s.n, tv);
+    v[0] = (double)norm2(tv);
+  }
+  double tot[1];
+  if (chain_reduce<1>(v, a.partials, a.counters, g, ci, c_, tot) && threadIdx.x == 0) {
+    const double pAp = tot[0];
+    if (pAp > 0.0 && isfinite(pAp)) {
+      cc->alpha = cc->rr / pAp;
+    } else {  // breakdown: leave the chain with its current iterate
+      cc->alpha = 0.0;
+      cc->flags |= 2;
+      cc->state = 0;
+      atomicSub(a.n_active, 1);
+    }
+  }
+}
+
+// Kernel B: A p = D^dag t; x += alpha p; r -= alpha A p; beta; convergence.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_cg_b(Geo g, CgArgs<R> a) {
+  CHAIN_PROLOGUE
+  if (cc->state != 1) return;
+  const Site s = site_of(g, ci, c_);
+  const R* __restrict__ pnew = cc->par ? a.pa : a.pb;
+  const R alpha = (R)cc->alpha;
+  double v[1] = {0.0};
+  if (s.valid) {
+    const long long nxm = at(s, xm1(s), s.t), ntm = at(s, s.x, tm1(s));
+    const Lk<R> u = ld_lk(a.U, s.n);
+    const Sp<R> o = hop_sum<true, R>(ld_sp(a.t, at(s, xp1(s), s.t)), ld_sp(a.t, nxm),
+                                     ld_sp(a.t, at(s, s.x, tp1(s))), ld_sp(a.t, ntm), u.x,
+                                     ld_lk(a.U, nxm).x, u.t, ld_lk(a.U, ntm).t);
+    const Sp<R> Ap = (R)(2.0 + ci.m0) * ld_sp(a.t, s.n) - (R)0.5 * o;
+    const Sp<R> pv = ld_sp(pnew, s.n);
+    st_sp(a.x, s.n, ld_sp_cg(a.x, s.n) + alpha * pv);
+    const Sp<R> rv = ld_sp_cg(a.r, s.n) - alpha * Ap;
+    st_sp(a.r, s.n, rv);
+    v[0] = (double)norm2(rv);
+  }
+  double tot[1];
+  if (chain_reduce<1>(v, a.partials, a.counters, g, ci, c_, tot) && threadIdx.x == 0) {
+    const double rr = tot[0];
+    cc->rr_prev = cc->rr;
+    cc->rr = rr;
+    cc->beta = rr / cc->rr_prev;
+    cc->par ^= 1;
+    cc->iters += 1;
+    const bool conv = rr <= a.tol2 * cc->bb;
+    if (!isfinite(rr)) {
+      cc->flags |= 2;
+      cc->state = 0;
+      atomicSub(a.n_active, 1);
+    } else if (a.mixed) {
+      if (conv || cc->iters >= a.maxit) {
+        cc->state = 2;  // wait for the FP64 check
+        cc->need_update = 1;
+      } else if (rr < a.delta2 * cc->rmax) {
+        cc->need_update = 1;
+      }
+      cc->rmax = fmax(cc->rmax, rr);
+    } else if (conv) {
+      cc->state = 0;
+      atomicSub(a.n_active, 1);
+    } else if (cc->iters >= a.maxit) {
+      cc->flags |= 1;
+      cc->state = 0;
+      atomicSub(a.n_active, 1);
+    }
+  }
+}
+
+// FP64 residual, step 1: t64 = D (xhi + x), for chains that asked for a
+// reliable update (all chains if `all`).  x may be NULL.
+__global__ void __launch_bounds__(kBlock) k_cg_res_d(Geo g, CgArgs<float> a, const double* xhi,
+                                                     const float* x, int all) {
+  CHAIN_PROLOGUE
+  if (!all && !cc->need_update) return;
+  const Site s = site_of(g, ci, c_);
+  if (!s.valid) return;
+  auto X = [&](long long m) {
+    Sp<double> v = ld_sp(xhi, m);
+    if (x) v = v + to_d(ld_sp(x, m));
+    return v;
+  };
+  const long long nxm = at(s, xm1(s), s.t), ntm = at(s, s.x, tm1(s));
+  const Lk<double> u = ld_lk(a.U64, s.n);
+  const Sp<double> o =
+      hop_sum<false, double>(X(at(s, xp1(s), s.t)), X(nxm), X(at(s, s.x, tp1(s))), X(ntm), u.x,
+                             ld_lk(a.U64, nxm).x, u.t, ld_lk(a.U64, ntm).t);
+  st_sp(a.t64, s.n, (2.0 + ci.m0) * X(s.n) - 0.5 * o);
+}
+
+// FP64 residual, step 2: r = b - D^dag t64 and |r|^2.  In update mode
+// (!all) also xhi += x, x = 0, r32 = r, and the chain's state advances; in
+// report mode only rr_true is written.
+__global__ void __launch_bounds__(kBlock) k_cg_res_r(Geo g, CgArgs<float> a, double* xhi,
+                                                     int all) {
+  CHAIN_PROLOGUE
+  if (!all && !cc->need_update) return;
+  const Site s = site_of(g, ci, c_);
+  double v[1] = {0.0};
+  if (s.valid) {
+    const long long nxm = at(s, xm1(s), s.t), ntm = at(s, s.x, tm1(s));
+    const Lk<double> u = ld_lk(a.U64, s.n);
+    const Sp<double> o =
+        hop_sum<true, double>(ld_sp(a.t64, at(s, xp1(s), s.t)), ld_sp(a.t64, nxm),
+                              ld_sp(a.t64, at(s, s.x, tp1(s))), ld_sp(a.t64, ntm), u.x,
+                              ld_lk(a.U64, nxm).x, u.t, ld_lk(a.U64, ntm).t);
+    const Sp<double> Ax = (2.0 + ci.m0) * ld_sp(a.t64, s.n) - 0.5 * o;
+    const Sp<double> r = ld_sp(a.b, s.n) - Ax;
+    v[0] = norm2(r);
+    if (!all) {
+      st_sp(xhi, s.n, ld_sp_cg(xhi, s.n) + to_d(ld_sp_cg(a.x, s.n)));
+      st_sp(a.x, s.n, Sp<float>{{0, 0}, {0, 0}});
+      st_sp(a.r, s.n, to_r<float>(r));
+    }
+  }
+  double tot[1];
+  if (chain_reduce<1>(v, a.partials, a.counters, g, ci, c_, tot) && threadIdx.x == 0) {
+    const double rr = tot[0];
+    cc->rr_true = rr;
+    if (!all) {
+      cc->need_update = 0;
+      cc->rmax = rr;
+      if (!isfinite(rr)) {
+        cc->flags |= 2;
+        cc->state = 0;
+        atomicSub(a.n_active, 1);
+      } else if (rr <= a.tol2 * cc->bb) {
+        cc->state = 0;
+        atomicSub(a.n_active, 1);
+      } else if (cc->iters >= a.maxit) {
+        cc->flags |= 1;
+        cc->state = 0;
+        atomicSub(a.n_active, 1);
+      } else {
+        cc->beta = rr / cc->rr_prev;
+        cc->rr = rr;
+        cc->state = 1;
+      }
+    }
+  }
+}
+
+// CG kernel timing (sm_profile_enable / sm_profile_read).
+struct Profile {
+  bool on = false;
+  bool ready = false;
+  cudaEvent_t e0[2], e1[2], e2[2];  // chunk start, after iterations, after residual
+  double iter_ms = 0, res_ms = 0;
+  long long batched = 0, site_iters = 0;
+};
+static Profile g_prof;
+
+static int prof_record(cudaEvent_t* e, int slot, cudaStream_t s) {
+  if (!g_prof.on) return SM_OK;
+  SM_CU(cudaEventRecord(e[slot], s));
+  return SM_OK;
+}
+
+// After chunk `slot` is known complete: add its kernel times.
+static int prof_collect(int slot, bool residual) {
+  if (!g_prof.on) return SM_OK;
+  float a = 0.f, b = 0.f;
+  SM_CU(cudaEventElapsedTime(&a, g_prof.e0[slot], g_prof.e1[slot]));
+  g_prof.iter_ms += a;
+  if (residual) {
+    SM_CU(cudaEventElapsedTime(&b, g_prof.e1[slot], g_prof.e2[slot]));
+    g_prof.res_ms += b;
+  }
+  return SM_OK;
+}
+
+template <typename R>
+static int iterate(Ctx& c, CgArgs<R>& a, int n) {
+  for (int k = 0; k < n; ++k) {
+    k_cg_a<R><<<c.grid(), kBlock, 0, c.s>>>(c.g, a);
+    int rc = launched(c.st, "cg_a");
+    if (rc) return rc;
+    k_cg_b<R><<<c.grid(), kBlock, 0, c.s>>>(c.g, a);
+    rc = launched(c.st, "cg_b");
+    if (rc) return rc;
+  }
+  return SM_OK;
+}
+
+static int residual(Ctx& c, CgArgs<float>& a, double* xhi, const float* x, int all) {
+  k_cg_res_d<<<c.grid(), kBlock, 0, c.s>>>(c.g, a, xhi, x, all);
+  int rc = launched(c.st, "cg_res_d");
+  if (rc) return rc;
+  k_cg_res_r<<<c.grid(), kBlock, 0, c.s>>>(c.g, a, xhi, all);
+  return launched(c.st, "cg_res_r");
+}
+
+// The host loop keeps one chunk of iterations in flight: it enqueues chunk
+// k+1 before it waits for the active-chain count written after chunk k.
+// Iterations enqueued after a chain has converged exit at once.
+template <typename R>
+static int run(Ctx& c, CgArgs<R>& a, CgArgs<float>& af, int chunk, int maxit, long long* batched,
+               long long* updates) {
+  int* h = c.L->h_pinned;
+  int it = 0, k = 0;
+  const int max_chunks = maxit / chunk + 2;
+  auto enqueue = [&](int slot) -> int {
+    int rc = prof_record(g_prof.e0, slot, c.s);
+    if (rc) return rc;
+    rc = iterate<R>(c, a, chunk);
+    if (rc) return rc;
+    if ((rc = prof_record(g_prof.e1, slot, c.s))) return rc;
+    it += chunk;
+    if (a.mixed) {
+      rc = residual(c, af, af.xhi, af.x, 0);
+      if (rc) return rc;
+      (*updates)++;
+    }
+    if ((rc = prof_record(g_prof.e2, slot, c.s))) return rc;
+    SM_CU(cudaMemcpyAsync(h + slot, a.n_active, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+    SM_CU(cudaEventRecord(c.L->ev[slot], c.s));
+    return SM_OK;
+  };
+  int rc = enqueue(0);
+  if (rc) return rc;
+  for (k = 0; k < max_chunks; ++k) {
+    const int slot = k & 1;
+    rc = enqueue(slot ^ 1);
+    if (rc) return rc;
+    SM_CU(cudaEventSynchronize(c.L->ev[slot]));
+    if ((rc = prof_collect(slot, a.mixed != 0))) return rc;
+    if (h[slot] == 0) break;
+  }
+  SM_CU(cudaStreamSynchronize(c.s));
+  if ((rc = prof_collect((k + 1) & 1, a.mixed != 0))) return rc;
+  *batched += it;
+  return SM_OK;
+}
+
+int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
+             const sm_cg_params& cg, int* iters, double* relres) {
+  if (!U64 || !b || !x) return fail(SM_ERR_ARG, "cg_solve: NULL field");
+  if (!(cg.tol > 0.0) || cg.maxit < 1) return fail(SM_ERR_ARG, "cg_solve: bad tol or maxit");
+  const bool mixed = cg.prec == SM_MIXED;
+  if (!mixed && cg.prec != SM_F64) return fail(SM_ERR_ARG, "cg_solve: prec must be F64 or MIXED");
+  if (mixed && (!U32 || !(cg.delta > 0.0 && cg.delta < 1.0)))
+    return fail(SM_ERR_ARG, "cg_solve: MIXED needs U32 and 0 < delta < 1");
+  if (b == x) return fail(SM_ERR_ARG, "cg_solve: b and x alias");
+
+  CgArgs<float> af{};
+  af.U = U32;
+  af.U64 = U64;
+  af.b = b;
+  af.r = c.w.r32;
+  af.x = c.w.x32;
+  af.pa = c.w.p32a;
+  af.pb = c.w.p32b;
+  af.t = c.w.t32;
+  af.xhi = x;
+  af.t64 = c.w.t;
+  af.cgc = c.w.cgc;
+  af.partials = c.w.partials;
+  af.counters = c.w.counters;
+  af.n_active = c.w.n_active;
+  af.tol2 = cg.tol * cg.tol;
+  af.delta2 = cg.delta * cg.delta;
+  af.maxit = cg.maxit;
+  af.mixed = mixed ? 1 : 0;
+
+  SM_CU(cudaMemsetAsync(c.w.n_active, 0, sizeof(int), c.s));
+  long long batched = 0, updates = 0;
+  int rc;
+  const int chunk = 8;
+  if (mixed) {
+    k_cg_init<float><<<c.grid(), kBlock, 0, c.s>>>(c.g, af);
+    if ((rc = launched(c.st, "cg_init"))) return rc;
+    if ((rc = run<float>(c, af, af, chunk, cg.maxit, &batched, &updates))) return rc;
+  } else {
+    CgArgs<double> ad{};
+    ad.U = U64;
+    ad.U64 = U64;
+    ad.b = b;
+    ad.r = c.w.r;
+    ad.x = x;
+    ad.pa = c.w.p0;
+    ad.pb = c.w.p1;
+    ad.t = c.w.t;
+    ad.xhi = nullptr;
+    ad.t64 = c.w.t;
+    ad.cgc = c.w.cgc;
+    ad.partials = c.w.partials;
+    ad.counters = c.w.counters;
+    ad.n_active = c.w.n_active;
+    ad.tol2 = af.tol2;
+    ad.delta2 = af.delta2;
+    ad.maxit = cg.maxit;
+    ad.mixed = 0;
+    k_cg_init<double><<<c.grid(), kBlock, 0, c.s>>>(c.g, ad);
+    if ((rc = launched(c.st, "cg_init"))) return rc;
+    if ((rc = run<double>(c, ad, af, chunk, cg.maxit, &batched, &updates))) return rc;
+    // report the FP64 true residual of the result
+    if ((rc = residual(c, af, x, nullptr, 1))) return rc;
+  }
+  std::vector<CgChain> h(c.L->nchains);
+  SM_CU(cudaMemcpyAsync(h.data(), c.w.cgc, sizeof(CgChain) * h.size(), cudaMemcpyDeviceToHost, c.s));
+  SM_CU(cudaStreamSynchronize(c.s));
+  c.st->cg_solves++;
+  c.st->cg_iterations += batched;
+  if (g_prof.on) {
+    g_prof.batched += batched;
+    for (int i = 0; i < c.L->nchains; ++i)
+      g_prof.site_iters += (long long)h[i].iters * c.L->chains[i].L * c.L->chains[i].T;
+  }
+  c.st->reliable_updates += updates;
+  int worst = SM_OK;
+  if (!c.strict && c.chain_flags.size() != h.size()) c.chain_flags.assign(h.size(), 0);
+  for (int i = 0; i < c.L->nchains; ++i) {
+    if (!c.strict) c.chain_flags[i] |= h[i].flags;
+    c.st->chain_iterations += h[i].iters;
+    if (iters) iters[i] = h[i].iters;
+    if (relres) relres[i] = h[i].bb > 0 ? std::sqrt(h[i].rr_true / h[i].bb) : 0.0;
+    if (h[i].flags & 2) worst = SM_ERR_NAN;
+    else if ((h[i].flags & 1) && worst == SM_OK) worst = SM_ERR_NOT_CONVERGED;
+  }
+  if (!c.strict) return SM_OK;
+  if (worst == SM_ERR_NAN) return fail(SM_ERR_NAN, "cg_solve: breakdown or non-finite residual");
+  if (worst == SM_ERR_NOT_CONVERGED) return fail(SM_ERR_NOT_CONVERGED, "cg_solve: maxit reached");
+  return SM_OK;
+}
+
+}  // namespace sm
+
+using namespace sm;
+
+extern "C" int sm_profile_enable(int on) {
+  if (on && !g_prof.ready) {
+    for (int i = 0; i < 2; ++i) {
+      SM_CU(cudaEventCreate(&g_prof.e0[i]));
+      SM_CU(cudaEventCreate(&g_prof.e1[i]));
+      SM_CU(cudaEventCreate(&g_prof.e2[i]));
+    }
+    g_prof.ready = true;
+  }
+  g_prof.on = on != 0;
+  return SM_OK;
+}
+
+extern "C" int sm_profile_read(double* iter_ms, double* res_ms, long long* batched_iters,
+                               long long* site_iters, int reset) {
+  if (iter_ms) *iter_ms = g_prof.iter_ms;
+  if (res_ms) *res_ms = g_prof.res_ms;
+  if (batched_iters) *batched_iters = g_prof.batched;
+  if (site_iters) *site_iters = g_prof.site_iters;
+  if (reset) {
+    g_prof.iter_ms = g_prof.res_ms = 0;
+    g_prof.batched = g_prof.site_iters = 0;
+  }
+  return SM_OK;
+}
+
+extern "C" int sm_cg_solve(const sm_lattice* lat, const double* U64, const float* U32,
+                           const double* b, double* x, const sm_cg_params* cg, void* ws,
+                           size_t ws_bytes, int* iters, double* relres, void* stream) {
+  Ctx c;
+  int rc = c.init(lat, ws, ws_bytes, stream, nullptr);
+  if (rc) return rc;
+  if (!cg) return fail(SM_ERR_ARG, "sm_cg_solve: cg is NULL");
+  return cg_solve(c, U64, U32, b, x, *cg, iters, relres);
+}

@@ -1,0 +1,310 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Every comparison is element by element on seeded inputs.  Batches are
+ragged (chains of different L x T, beta, kappa, including odd sides and the
+smallest 2 x 2 lattice) so that several site blocks, a partial last block and
+the chain boundaries are exercised.
+
+Tolerances.  FP64 operators and forces: 1e-12 relative (the target for the
+FP64 path; the arithmetic differs only in rounding order).  Solves run at
+CG tolerance 1e-14 so that solver truncation stays below that.  FP32
+operators: 2e-6 relative (a few FP32 ulps per hop sum).
+"""
+import numpy as np
+import pytest
+
+from oracle import integrators as ig
+from oracle import schwinger as sw
+from tests.gpu_util import Batch, rel_err
+
+pytestmark = pytest.mark.gpu
+
+DIMS = [(8, 8), (3, 5), (2, 2), (32, 16), (17, 9), (4, 6)]
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1512_03812_gb300 as P
+    P.build()
+    return t
+
+
+def cg(tol=1e-14, prec="f64", maxit=20000):
+    import paper_1512_03812_gb300 as P
+    return P.CG(tol=tol, maxit=maxit, prec=prec)
+
+
+def batch(torch, dims=DIMS, seed=0, betas=(2.0, 1.0, 4.0, 2.0, 1.5, 3.0), kappas=(0.24, 0.2, 0.22, 0.25, 0.21, 0.23)):
+    n = len(dims)
+    return Batch(dims, np.resize(betas, n), np.resize(kappas, n), seed=seed)
+
+
+def test_links(torch):
+    b = batch(torch)
+    q = b.q()
+    U64, U32 = b.lat.links(b.dev(q))
+    for c, ol in enumerate(b.olat):
+        U = sw.links(b.chain(q, c))
+        U[-1, :, 1] *= -1.0  # antiperiodic sign folded into the last t-links
+        assert rel_err(b.chain(U64, c), U) < 1e-15
+        assert rel_err(b.chain(U32, c), U) < 1e-7
+
+
+@pytest.mark.parametrize("dagger", [False, True])
+def test_apply_D_f64_and_f32(torch, dagger):
+    b = batch(torch)
+    q, psi = b.q(), b.spinor()
+    U64, U32 = b.lat.links(b.dev(q))
+    out64 = b.lat.apply_D(U64, b.dev(psi), dagger=dagger)
+    out32 = b.lat.apply_D(U32, b.dev(psi, torch.complex64), dagger=dagger)
+    for c, ol in enumerate(b.olat):
+        ref = sw.apply_D(ol, sw.links(b.chain(q, c)), b.chain(psi, c), dagger=dagger)
+        assert rel_err(b.chain(out64, c), ref) < 1e-14
+        assert rel_err(b.chain(out32, c), ref) < 2e-6
+
+
+def test_apply_DdagD(torch):
+    b = batch(torch)
+    q, psi = b.q(), b.spinor()
+    U64, U32 = b.lat.links(b.dev(q))
+    out = b.lat.apply_DdagD(U64, b.dev(psi))
+    out32 = b.lat.apply_DdagD(U32, b.dev(psi, torch.complex64))
+    for c, ol in enumerate(b.olat):
+        ref = sw.apply_DdagD(ol, sw.links(b.chain(q, c)), b.chain(psi, c))
+        assert rel_err(b.chain(out, c), ref) < 1e-14
+        assert rel_err(b.chain(out32, c), ref) < 4e-6
+
+
+def test_cg_f64_matches_oracle(torch):
+    b = batch(torch)
+    q, phi = b.q(), b.spinor()
+    U64, U32 = b.lat.links(b.dev(q))
+    x, iters, relres = b.lat.cg_solve(U64, U32, b.dev(phi), cg(1e-14))
+    assert (relres < 1e-13).all(), relres
+    for c, ol in enumerate(b.olat):
+        ref = sw.Solver(tol=1e-14).cg(ol, sw.links(b.chain(q, c)), b.chain(phi, c))
+        assert rel_err(b.chain(x, c), ref) < TOL64
+        assert iters[c] > 0
+
+
+def test_cg_mixed_reaches_fp64_true_residual(torch):
+    b = batch(torch)
+    q, phi = b.q(), b.spinor()
+    U64, U32 = b.lat.links(b.dev(q))
+    x64, _, _ = b.lat.cg_solve(U64, U32, b.dev(phi), cg(1e-12))
+    xm, iters, relres = b.lat.cg_solve(U64, U32, b.dev(phi), cg(1e-10, "mixed"))
+    assert (relres <= 1e-10).all(), relres
+    # an independent check of the residual with the FP64 operator
+    r = b.dev(phi) - b.lat.apply_DdagD(U64, xm)
+    for c in range(len(b.dims)):
+        rc = b.chain(r, c)
+        assert np.linalg.norm(rc) <= 1.0000001e-10 * np.linalg.norm(b.chain(phi, c))
+        assert rel_err(b.chain(xm, c), b.chain(x64, c)) < 1e-8
+
+
+def test_cg_zero_rhs_and_maxit(torch):
+    import paper_1512_03812_gb300 as P
+    b = batch(torch, dims=[(8, 8), (4, 4)])
+    U64, U32 = b.lat.links(b.dev(b.q()))
+    zero = torch.zeros((b.lat.N, 2), dtype=torch.complex128, device="cuda")
+    x, iters, relres = b.lat.cg_solve(U64, U32, zero, cg(1e-10))
+    assert (iters == 0).all() and float(x.abs().max()) == 0.0
+    with pytest.raises(P.NotConverged):
+        b.lat.cg_solve(U64, U32, b.dev(b.spinor()), cg(1e-14, maxit=3))
+    with pytest.raises(P.NotConverged):
+        b.lat.cg_solve(U64, U32, b.dev(b.spinor()), cg(1e-14, "mixed", maxit=3))
+
+
+def test_forces(torch):
+    b = batch(torch)
+    q, eta = b.q(), b.eta()
+    qd = b.dev(q)
+    U64, _ = b.lat.links(qd)
+    phi = b.lat.apply_D(U64, b.dev(eta), dagger=True)
+    FG = b.lat.gauge_force(qd)
+    Ff = b.lat.fermion_force(qd, phi, cg(1e-14))
+    Fa = b.lat.force(qd, phi, "full", cg(1e-14))
+    for c, ol in enumerate(b.olat):
+        U = sw.links(b.chain(q, c))
+        ph = sw.apply_D(ol, U, b.chain(eta, c), dagger=True)
+        assert rel_err(b.chain(phi, c), ph) < 1e-14
+        g = sw.gauge_force(ol, U)
+        f = sw.fermion_force(ol, U, ph, sw.Solver(1e-14))
+        assert rel_err(b.chain(FG, c), g) < TOL64
+        assert rel_err(b.chain(Ff, c), f) < TOL64
+        assert rel_err(b.chain(Fa, c), g + f) < TOL64
+
+
+@pytest.mark.parametrize("part", ["gauge", "fermion", "full"])
+def test_force_gradient(torch, part):
+    b = batch(torch)
+    q, eta = b.q(), b.eta()
+    qd = b.dev(q)
+    U64, _ = b.lat.links(qd)
+    phi = b.lat.apply_D(U64, b.dev(eta), dagger=True)
+    F = b.lat.field()
+    C = b.lat.force_gradient(qd, phi, part, cg(1e-14), F=F)
+    for c, ol in enumerate(b.olat):
+        U = sw.links(b.chain(q, c))
+        ph = sw.apply_D(ol, U, b.chain(eta, c), dagger=True)
+        Fo, Co = sw.force_and_gradient(ol, U, ph, sw.Solver(1e-14), part)
+        assert rel_err(b.chain(F, c), Fo) < TOL64
+        assert rel_err(b.chain(C, c), Co) < 1e-11
+
+
+@pytest.mark.parametrize("part", ["gauge", "fermion", "full"])
+def test_hvp(torch, part):
+    b = batch(torch)
+    q, eta, v = b.q(), b.eta(), b.v()
+    qd = b.dev(q)
+    U64, _ = b.lat.links(qd)
+    phi = b.lat.apply_D(U64, b.dev(eta), dagger=True)
+    Hv = b.lat.hvp(qd, phi, b.dev(v), part, cg(1e-14))
+    for c, ol in enumerate(b.olat):
+        U = sw.links(b.chain(q, c))
+        ph = sw.apply_D(ol, U, b.chain(eta, c), dagger=True)
+        s = sw.Solver(1e-14)
+        vc = b.chain(v, c)
+        ref = np.zeros_like(vc)
+        if part in ("gauge", "full"):
+            ref += 0.5 * sw.c_fg(ol, U, vc)
+        if part in ("fermion", "full"):
+            chi, xi = sw.chi_xi(ol, U, ph, s)
+            ref += 0.5 * sw.c_fermion(ol, U, chi, xi, vc, s)
+        assert rel_err(b.chain(Hv, c), ref) < 1e-11
+
+
+@pytest.mark.parametrize("part", ["gauge", "fermion", "full"])
+def test_shifted_force(torch, part):
+    b = batch(torch)
+    q, eta = b.q(), b.eta()
+    qd = b.dev(q)
+    U64, _ = b.lat.links(qd)
+    phi = b.lat.apply_D(U64, b.dev(eta), dagger=True)
+    h = 0.3
+    Fs = b.lat.fg_shifted_force(qd, phi, h, part, cg(1e-14))
+    for c, ol in enumerate(b.olat):
+        ph = sw.apply_D(ol, sw.links(b.chain(q, c)), b.chain(eta, c), dagger=True)
+        ref = sw.shifted_force(ol, b.chain(q, c), ph, sw.Solver(1e-14), h, part)
+        assert rel_err(b.chain(Fs, c), ref) < TOL64
+
+
+def test_energies(torch):
+    b = batch(torch)
+    q, p, eta = b.q(), b.p(), b.eta()
+    qd = b.dev(q)
+    U64, _ = b.lat.links(qd)
+    phi = b.lat.apply_D(U64, b.dev(eta), dagger=True)
+    e = b.lat.energies(qd, b.dev(p), phi, cg(1e-14))
+    for c, ol in enumerate(b.olat):
+        U = sw.links(b.chain(q, c))
+        assert abs(float(e["K"][c]) - sw.kinetic(b.chain(p, c))) < 1e-13 * ol.V
+        assert abs(float(e["SG"][c]) - sw.gauge_action(ol, U)) < 1e-13 * ol.V
+        # S_F at the heatbath equals eta^dag eta
+        en = float(np.vdot(b.chain(eta, c), b.chain(eta, c)).real)
+        assert abs(float(e["SF"][c]) - en) < 1e-11 * en
+
+
+SCHEMES = [("leapfrog", 1, "exact"), ("five_stage", 1, "exact"), ("five_stage_fg", 1, "exact"),
+           ("five_stage_fg", 1, "shifted"), ("nested_leapfrog", 2, "exact"),
+           ("nested_five_stage", 2, "exact"), ("nested_fg", 2, "exact"),
+           ("nested_fg", 2, "shifted"), ("adapted_nested_fg", 2, "exact"),
+           ("adapted_nested_fg", 2, "shifted")]
+
+
+@pytest.mark.parametrize("scheme,M,fg", SCHEMES)
+@pytest.mark.parametrize("merge", [True, False])
+def test_md_trajectory(torch, scheme, M, fg, merge):
+    import paper_1512_03812_gb300 as P
+    dims = [(8, 8), (6, 4), (5, 7)]
+    b = batch(torch, dims=dims)
+    q, p, eta = b.q(), b.p(), b.eta()
+    qd, pd = b.dev(q), b.dev(p)
+    U64, _ = b.lat.links(qd)
+    phi = b.lat.apply_D(U64, b.dev(eta), dagger=True)
+    md = P.MD(scheme=scheme, tau=0.5, n=2, M=M, fg=fg, merge_kicks=merge, cg=cg(1e-14))
+    b.lat.md_trajectory(qd, pd, phi, md)
+    for c, ol in enumerate(b.olat):
+        ph = sw.apply_D(ol, sw.links(b.chain(q, c)), b.chain(eta, c), dagger=True)
+        st = ig.State(ol, b.chain(q, c).copy(), b.chain(p, c).copy(), ph, sw.Solver(1e-14))
+        ig.md_trajectory(st, scheme, 0.5, 2, M=M, fg=fg)
+        assert rel_err(b.chain(qd, c), st.q) < TOL64
+        assert rel_err(b.chain(pd, c), st.p) < 1e-11
+
+
+@pytest.mark.parametrize("scheme,M,fg", [("leapfrog", 1, "exact"), ("five_stage", 1, "exact"),
+                                         ("five_stage_fg", 1, "exact"),
+                                         ("nested_five_stage", 2, "exact"),
+                                         ("adapted_nested_fg", 2, "exact"),
+                                         ("adapted_nested_fg", 2, "shifted")])
+def test_hmc_trajectory_parity(torch, scheme, M, fg):
+    """8x8, beta 2, kappa 0.24: Delta H to 1e-12 relative to H and identical
+    Metropolis decisions, over chains started from seeded hot links."""
+    import paper_1512_03812_gb300 as P
+    n_ch = 4
+    b = batch(torch, dims=[(8, 8)] * n_ch, betas=2.0, kappas=0.24, seed=5)
+    q, p, eta = b.q(), b.p(), b.eta()
+    us = np.linspace(0.05, 0.95, n_ch)
+    qd = b.dev(q)
+    md = P.MD(scheme=scheme, tau=1.0, n=5, M=M, fg=fg, cg=cg(1e-14))
+    q_md = torch.empty_like(qd)
+    dH, H0, acc = b.lat.hmc_trajectory(qd, b.dev(p), b.dev(eta), us, md, q_md=q_md)
+    for c, ol in enumerate(b.olat):
+        r = ig.hmc_trajectory(ol, b.chain(q, c), b.chain(p, c), b.chain(eta, c), us[c], scheme,
+                              1.0, 5, M=M, fg=fg, solver=sw.Solver(1e-14))
+        assert abs(dH[c] - r.dH) <= 1e-12 * max(1.0, abs(r.H0)), (dH[c], r.dH)
+        assert abs(H0[c] - r.H0) <= 1e-12 * abs(r.H0)
+        assert bool(acc[c]) == r.accepted
+        assert rel_err(b.chain(q_md, c), r.q_md) < TOL64
+        assert np.array_equal(b.chain(qd, c), r.q) or rel_err(b.chain(qd, c), r.q) < TOL64
+
+
+def test_batched_chain_equals_solo_run_bitwise(torch):
+    import paper_1512_03812_gb300 as P
+    dims = [(8, 8), (16, 8), (6, 6)]
+    b = batch(torch, dims=dims)
+    q, p, eta = b.q(), b.p(), b.eta()
+    md = P.MD(scheme="adapted_nested_fg", tau=0.5, n=2, M=2, cg=cg(1e-12))
+    qd = b.dev(q)
+    dH, _, _ = b.lat.hmc_trajectory(qd, b.dev(p), b.dev(eta), 0.5, md)
+    for c in range(len(dims)):
+        solo = P.Lattice(dims[c][0], dims[c][1], b.betas[c], b.m0[c])
+        sl = slice(b.off[c], b.off[c + 1])
+        qs = b.dev(q[sl])
+        dHs, _, _ = solo.hmc_trajectory(qs, b.dev(p[sl]), b.dev(eta[sl]), 0.5, md)
+        assert dHs[0] == dH[c]
+        assert torch.equal(qs, qd[sl])
+
+
+def test_determinism(torch):
+    import paper_1512_03812_gb300 as P
+    b = batch(torch)
+    q, p, eta = b.q(), b.p(), b.eta()
+    md = P.MD(scheme="nested_fg", tau=0.5, n=2, M=2, cg=cg(1e-12, "mixed"))
+    outs = []
+    for _ in range(2):
+        qd = b.dev(q)
+        dH, _, _ = b.lat.hmc_trajectory(qd, b.dev(p), b.dev(eta), 0.5, md)
+        outs.append((dH.copy(), qd.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_nonfinite_input_is_reported(torch):
+    import paper_1512_03812_gb300 as P
+    b = batch(torch, dims=[(8, 8), (8, 8)])
+    q, p, eta = b.q(), b.p(), b.eta()
+    p[b.off[1] + 3, 0] = np.nan  # poison chain 1 on the host
+    qd = b.dev(q)
+    md = P.MD(scheme="leapfrog", tau=0.2, n=2, cg=cg(1e-10))
+    dH, _, acc = b.lat.hmc_trajectory(qd, b.dev(p), b.dev(eta), 0.5, md, check=False)
+    assert np.isfinite(dH[0]) and not np.isfinite(dH[1])
+    assert not acc[1]
+    # the rejected chain got its starting links back
+    assert np.array_equal(b.chain(qd, 1), b.chain(q, 1))
+    with pytest.raises(P.SchwingerError):
+        b.lat.hmc_trajectory(b.dev(q), b.dev(p), b.dev(eta), 0.5, md)
