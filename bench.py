@@ -113,6 +113,31 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------ ranks --------
+
+def shard(world, rank, chains_per_rank):
+    """The chains of one rank: an independent batch with its own random
+    streams (the path shards as independent chains: weak scaling, no
+    data-path collective)."""
+    return {"seed": 1234 + 7919 * rank, "chains": chains_per_rank,
+            "first_chain": rank * chains_per_rank, "world": world}
+
+
+def max_over_ranks(x, dist=None, device=None):
+    """Max of a per-rank float over all ranks (the only collective)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
+def aggregate(world, chains_per_rank, steps, ms_max):
+    """Whole-job trajectories per second from the slowest rank's time."""
+    return world * chains_per_rank * steps / (ms_max / 1e3)
+
+
 # ------------------------------------------------------------ our arm ------
 
 def run_ours(args):
@@ -136,10 +161,11 @@ def run_ours(args):
     m0 = kappa_to_m0(W["kappa"])
     lat = P.Lattice([L] * B, [T] * B, W["beta"], m0, device=dev)
     N = lat.N
-    cgp = P.CG(tol=W["cg_tol"], maxit=20000, prec=args.prec)
+    W = dict(W, n=args.n, M=args.M)
+    cgp = P.CG(tol=W["cg_tol"], maxit=20000, prec=args.prec, delta=args.delta, algo=args.algo)
     md = P.MD(scheme=W["scheme"], tau=W["tau"], n=W["n"], M=W["M"], fg=W["fg"], cg=cgp)
     gen = torch.Generator(device=dev)
-    gen.manual_seed(1234 + 7919 * rank)
+    gen.manual_seed(shard(world, rank, B)["seed"])
 
     def draws(k):
         p = torch.randn((k, N, 2), generator=gen, device=dev, dtype=torch.float64)
@@ -148,22 +174,33 @@ def run_ours(args):
         u = torch.rand((k, B), generator=gen, device=dev, dtype=torch.float64).cpu().numpy()
         return p, e, u
 
-    # thermalise one configuration (chain 0 of a 1-chain lattice), untimed
+    # thermalise one configuration, untimed: first with heavy fermions
+    # (kappa 0.10: cheap, stable), then at the working kappa with small steps
     t0 = time.time()
-    one = P.Lattice(L, T, W["beta"], m0, device=dev)
     q1 = torch.zeros((L * T, 2), dtype=torch.float64, device=dev)
     g1 = torch.Generator(device=dev)
     g1.manual_seed(99)
-    md_th = P.MD(scheme="nested_leapfrog", tau=1.0, n=6, M=4, cg=P.CG(1e-8, 20000, "mixed"))
     acc_th = []
-    for _ in range(args.therm):
-        p = torch.randn((L * T, 2), generator=g1, device=dev, dtype=torch.float64)
-        e = torch.view_as_complex(torch.randn((L * T, 2, 2), generator=g1, device=dev,
-                                              dtype=torch.float64) * math.sqrt(0.5)).contiguous()
-        u = float(torch.rand(1, generator=g1, device=dev, dtype=torch.float64))
-        dH, _, acc = one.hmc_trajectory(q1, p, e, u, md_th)
-        acc_th.append(bool(acc[0]))
-    log(f"thermalised {args.therm} trajectories in {time.time() - t0:.1f}s, acc {np.mean(acc_th):.2f}")
+    # burn-in with forced acceptance (u = 0 accepts every finite Delta H),
+    # fine steps: heavy fermions first, then the working kappa
+    fine = P.CG(1e-8, 20000, "mixed")
+    phases = [(0.10, P.MD(scheme="nested_leapfrog", tau=1.0, n=5, M=8, cg=fine), args.therm, 0.0),
+              (W["kappa"], P.MD(scheme="nested_leapfrog", tau=1.0, n=16, M=4, cg=fine),
+               max(2, args.therm // 2), 0.0),
+              (W["kappa"], P.MD(scheme="nested_leapfrog", tau=1.0, n=16, M=4, cg=fine),
+               max(2, args.therm // 4), None)]
+    for kap, mdt, ntraj, uforce in phases:
+        one = P.Lattice(L, T, W["beta"], kappa_to_m0(kap), device=dev)
+        for _ in range(ntraj):
+            p = torch.randn((L * T, 2), generator=g1, device=dev, dtype=torch.float64)
+            e = torch.view_as_complex(torch.randn((L * T, 2, 2), generator=g1, device=dev,
+                                                  dtype=torch.float64) * math.sqrt(0.5))
+            u = float(torch.rand(1, generator=g1, device=dev, dtype=torch.float64))
+            u = u if uforce is None else uforce
+            dH, _, acc = one.hmc_trajectory(q1, p, e.contiguous(), u, mdt, check=False)
+            acc_th.append((kap, bool(acc[0]), float(dH[0])))
+    log(f"thermalised in {time.time() - t0:.1f}s: " +
+        " ".join(f"k{k:.2f}:{'A' if a else 'r'}{d:+.2g}" for k, a, d in acc_th))
     q_start = q1.repeat(B, 1).contiguous()
 
     flush = torch.empty(int(256 * 2 ** 20), dtype=torch.uint8, device=dev)
@@ -196,6 +233,7 @@ def run_ours(args):
         dH, _, acc = step(q, pk[i], ek[i], uk[i])
         dHs.append(dH)
         accs.append(acc)
+    st = lat.stats.as_dict()
     ev1.record()
     torch.cuda.synchronize()
     if world > 1:
@@ -204,13 +242,11 @@ def run_ours(args):
     clk = clocks.stop()
     launches = binding.launch_count() - n0
     prof = binding.profile_read(reset=True)
+    log(f"timed {K} steps: {ms / K:.1f} ms/step, last-step stats {st}, "
+        f"dH[:8] {np.round(dHs[-1][:8], 4)}")
     binding.profile_enable(False)
-    ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t)
-    traj_per_s = world * B * K / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dist, dev)
+    traj_per_s = aggregate(world, B, K, ms_max)
     acc_rate = float(np.mean(np.concatenate(accs)))
 
     # end to end through the public API with host buffers: per step the
@@ -230,11 +266,7 @@ def run_ours(args):
         step(q, pd, ed, uk[i])
     e1.record()
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     h2d = int(pd.numel() * 8 + ed.numel() * 16 + B * 8)
     d2h = int(B * (8 + 8 + 4))
 
@@ -242,7 +274,7 @@ def run_ours(args):
     fp64 = None
     if args.fp64_steps > 0:
         md64 = P.MD(scheme=W["scheme"], tau=W["tau"], n=W["n"], M=W["M"], fg=W["fg"],
-                    cg=P.CG(tol=W["cg_tol"], maxit=20000, prec="f64"))
+                    cg=P.CG(tol=W["cg_tol"], maxit=20000, prec="f64", algo=args.algo))
         q64 = q_start.clone()
         qm = q_start.clone()
         dev_max = 0.0
@@ -293,7 +325,7 @@ def run_ours(args):
         "config": dict(W, chains_per_gpu=B, precision=args.prec, parallelism=f"replicas{world}",
                        l2="flushed between steps (256 MiB write)"),
         "acceptance": round(acc_rate, 4),
-        "e2e": {"value": round(world * B * K / (e2e_ms / 1e3), 3), "unit": "trajectories/s",
+        "e2e": {"value": round(aggregate(world, B, K, e2e_ms), 3), "unit": "trajectories/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roofline,
@@ -360,6 +392,10 @@ def main():
     ap.add_argument("--therm", type=int, default=20)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--n", type=int, default=WORKLOAD["n"])
+    ap.add_argument("--M", type=int, default=WORKLOAD["M"])
+    ap.add_argument("--delta", type=float, default=0.1)
+    ap.add_argument("--algo", default="auto", choices=["auto", "grid", "chain"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

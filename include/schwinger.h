@@ -88,17 +88,25 @@ extern "C" {
 
 typedef struct sm_lattice sm_lattice;
 
+/* how a batched CG solve is laid out on the GPU */
+#define SM_CG_AUTO 0   /* chain-resident when every chain fits, else grid-wide */
+#define SM_CG_GRID 1   /* all chains advance together, two launches per iteration */
+#define SM_CG_CHAIN 2  /* one thread block owns one chain's whole solve; FP32 fields in
+                          shared memory (chains of at most 4096 sites for SM_MIXED,
+                          16384 for SM_F64) */
+
 /* CG parameters.  The solve of D^dag D x = b starts from x = 0 and stops, per
  * chain, when |b - D^dag D x| <= tol |b|: for SM_F64 the recursive residual
  * is tested, for SM_MIXED the FP64 true residual recomputed at each reliable
  * update.  A reliable update is taken when the FP32 residual has fallen by
- * the factor `delta` (0 < delta < 1) since the last one.  maxit bounds the
- * iterations of every chain. */
+ * the factor `delta` (0 < delta < 1) below its largest value since the last
+ * one.  maxit bounds the iterations of every chain. */
 typedef struct {
   double tol;
   int maxit;
   int prec;      /* SM_F64 or SM_MIXED */
   double delta;  /* reliable-update factor, e.g. 0.1 (SM_MIXED only) */
+  int algo;      /* SM_CG_AUTO, SM_CG_GRID or SM_CG_CHAIN */
 } sm_cg_params;
 
 /* One molecular-dynamics trajectory: n steps of size h = tau / n of `scheme`;

@@ -52,7 +52,7 @@ class NotConverged(SchwingerError):
 
 class CgParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("prec", ctypes.c_int),
-                ("delta", ctypes.c_double)]
+                ("delta", ctypes.c_double), ("algo", ctypes.c_int)]
 
 
 class MdParams(ctypes.Structure):
@@ -163,10 +163,11 @@ class CG:
     maxit: int = 20000
     prec: str = "f64"      # "f64" or "mixed"
     delta: float = 0.1
+    algo: str = "auto"     # "auto", "grid" (all chains in lockstep) or "chain" (block per chain)
 
     def c(self) -> CgParams:
         return CgParams(self.tol, self.maxit, {"f64": SM_F64, "mixed": SM_MIXED}[self.prec],
-                        self.delta)
+                        self.delta, {"auto": 0, "grid": 1, "chain": 2}[self.algo])
 
 
 @dataclass
@@ -321,8 +322,8 @@ class Lattice:
 
     def hmc_trajectory(self, q, p0, eta, u, md: MD, p_out=None, q_md=None, check=True):
         """One HMC update of every chain; returns (dH, H0, accepted) as numpy
-        arrays.  With check=False a non-finite Delta H is reported in dH
-        (and rejected) instead of raising."""
+        arrays.  With check=False, chains with a non-finite Delta H or a
+        failed solve are reported (rejected) instead of raising."""
         u = np.ascontiguousarray(np.broadcast_to(np.asarray(u, dtype=np.float64),
                                                  (self.nchains,)))
         dH = np.zeros(self.nchains)
@@ -333,7 +334,7 @@ class Lattice:
                                     ctypes.byref(m), *self._ws(), dH.ctypes.data,
                                     H0.ctypes.data, acc.ctypes.data, _ptr(p_out), _ptr(q_md),
                                     ctypes.byref(self.stats), _stream())
-        if check or rc != SM_ERR_NAN:
+        if check or rc not in (SM_ERR_NAN, SM_ERR_NOT_CONVERGED):
             _check(rc)
         return dH, H0, acc.astype(bool)
 

@@ -1,0 +1,402 @@
+// cg_chain.cu -- chain-resident conjugate gradient: one thread block owns one
+// chain's entire solve of D^dag D x = b.
+//
+// For batches of small lattices the grid-wide CG of solver.cu advances all
+// chains in lockstep and pays two launches per iteration.  Here every chain
+// iterates on its own block with only block barriers, so chains converge
+// independently and the whole solve is one launch.  In the FP32 form the links
+// U, the search direction p and t = D p live in shared memory (48 bytes per
+// site: 192 KB for a 64 x 64 lattice) and the iterate x and residual r in
+// registers, so an iteration touches no global memory at all.  The FP64
+// reliable update (x_hi += x; r = b - D^dag D x_hi) reads and writes the
+// FP64 fields in global memory.  In the FP64 form all fields stay in global
+// memory (L2-resident for small chains) and the block still iterates alone.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sm {
+
+constexpr int kChainThreads = 1024;
+
+struct ChainCgArgs {
+  const ChainInfo* chains;
+  const int* list;     // chains handled by this launch, one per block
+  const float* U32;
+  const double* U64;
+  const double* b;
+  double* x;           // FP64 solution (global)
+  double* t64;         // FP64 scratch [N][2][2]
+  double* r64;         // FP64 residual (FP64 form) [N][2][2]
+  double* p64;         // FP64 search direction (FP64 form)
+  CgChain* cgc;
+  double tol2, delta2;
+  int maxit;
+};
+
+// Sum over the block, returned to every thread.
+__device__ __forceinline__ double cta_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();  // red may still be read from the previous sum
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    s = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// Coordinates and neighbours of local site l of an L x T chain.
+struct Nb {
+  int l, xp, xm, tp, tm;  // local indices of n, n+x, n-x, n+t, n-t
+};
+__device__ __forceinline__ Nb neighbours(int l, int L, int T, int lshift) {
+  int x, t;
+  if (lshift >= 0) {
+    x = l & (L - 1);
+    t = l >> lshift;
+  } else {
+    t = l / L;
+    x = l - t * L;
+  }
+  const int row = t * L;
+  Nb n;
+  n.l = l;
+  n.xp = row + (x + 1 == L ? 0 : x + 1);
+  n.xm = row + (x == 0 ? L - 1 : x - 1);
+  n.tp = (t + 1 == T ? 0 : t + 1) * L + x;
+  n.tm = (t == 0 ? T - 1 : t - 1) * L + x;
+  return n;
+}
+
+__device__ __forceinline__ Sp<float> sp_of(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
+__device__ __forceinline__ float4 f4_of(Sp<float> s) {
+  return make_float4(s.a.re, s.a.im, s.b.re, s.b.im);
+}
+__device__ __forceinline__ Sp<double> to_dbl(Sp<float> v) {
+  return {{v.a.re, v.a.im}, {v.b.re, v.b.im}};
+}
+__device__ __forceinline__ Sp<float> to_flt(Sp<double> v) {
+  return {{(float)v.a.re, (float)v.a.im}, {(float)v.b.re, (float)v.b.im}};
+}
+
+// D (or D^dag) at one site of a field held in shared memory (FP32).
+template <bool DAG>
+__device__ __forceinline__ Sp<float> dslash_smem(const float4* __restrict__ f,
+                                                 const float4* __restrict__ U, const Nb& n,
+                                                 float diag) {
+  const float4 u = U[n.l];
+  const float4 uxm = U[n.xm], utm = U[n.tm];
+  const Sp<float> o = hop_sum<DAG, float>(sp_of(f[n.xp]), sp_of(f[n.xm]), sp_of(f[n.tp]),
+                                          sp_of(f[n.tm]), {u.x, u.y}, {uxm.x, uxm.y},
+                                          {u.z, u.w}, {utm.z, utm.w});
+  return diag * sp_of(f[n.l]) - 0.5f * o;
+}
+
+// D (or D^dag) at one site of an FP64 field in global memory; `off` is the
+// chain's first global site.
+template <bool DAG>
+__device__ __forceinline__ Sp<double> dslash_glob(const double* __restrict__ f,
+                                                  const double* __restrict__ U, long long off,
+                                                  const Nb& n, double diag) {
+  const Lk<double> u = ld_lk(U, off + n.l);
+  const Sp<double> o = hop_sum<DAG, double>(
+      ld_sp_cg(f, off + n.xp), ld_sp_cg(f, off + n.xm), ld_sp_cg(f, off + n.tp),
+      ld_sp_cg(f, off + n.tm), u.x, ld_lk(U, off + n.xm).x, u.t, ld_lk(U, off + n.tm).t);
+  return diag * ld_sp_cg(f, off + n.l) - 0.5 * o;
+}
+
+// FP64 true residual of the chain: t64 = D x, r = b - D^dag t64.  Returns
+// |r|^2 (to every thread); writes r into r64 if it is not NULL and calls
+// put(k, r) for each of the thread's sites.
+template <typename Put>
+__device__ __forceinline__ double true_residual(const ChainCgArgs& a, const ChainInfo& ci,
+                                                int lshift, double* red, Put put) {
+  const int V = ci.L * ci.T;
+  const double diag = 2.0 + ci.m0;
+  for (int l = threadIdx.x; l < V; l += blockDim.x) {
+    const Nb n = neighbours(l, ci.L, ci.T, lshift);
+    st_sp(a.t64, ci.off + l, dslash_glob<false>(a.x, a.U64, ci.off, n, diag));
+  }
+  __syncthreads();
+  double v = 0.0;
+  int k = 0;
+  for (int l = threadIdx.x; l < V; l += blockDim.x, ++k) {
+    const Nb n = neighbours(l, ci.L, ci.T, lshift);
+    const Sp<double> r = ld_sp_cg(a.b, ci.off + l) - dslash_glob<true>(a.t64, a.U64, ci.off, n, diag);
+    v += norm2(r);
+    put(k, l, r);
+  }
+  return cta_sum(v, red);
+}
+
+// Mixed precision: FP32 iterations in shared memory and registers, FP64
+// reliable updates.  SPT sites per thread (V <= SPT * blockDim.x).
+template <int SPT>
+__global__ void __launch_bounds__(kChainThreads, 1) k_cg_chain_mixed(ChainCgArgs a) {
+  extern __shared__ float4 smem[];
+  __shared__ double red[33];
+  const int c = a.list[blockIdx.x];
+  const ChainInfo ci = a.chains[c];
+  CgChain* cc = a.cgc + c;
+  const int V = ci.L * ci.T;
+  const int lshift = (ci.L & (ci.L - 1)) == 0 ? __ffs(ci.L) - 1 : -1;
+  float4* Us = smem;
+  float4* ps = smem + V;
+  float4* ts = smem + 2 * V;
+  const float diag = (float)(2.0 + ci.m0);
+
+  Sp<float> x[SPT], r[SPT];
+  double bb = 0.0;
+#pragma unroll
+  for (int k = 0; k < SPT; ++k) {
+    const int l = threadIdx.x + k * blockDim.x;
+    x[k] = {{0.f, 0.f}, {0.f, 0.f}};
+    r[k] = x[k];
+    if (l < V) {
+      Us[l] = __ldg(reinterpret_cast<const float4*>(a.U32) + ci.off + l);
+      const Sp<double> bv = ld_sp(a.b, ci.off + l);
+      bb += norm2(bv);
+      r[k] = to_flt(bv);
+      ps[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+      st_sp(a.x, ci.off + l, Sp<double>{{0, 0}, {0, 0}});
+    }
+  }
+  bb = cta_sum(bb, red);
+  double rr = bb, rr_prev = bb, rmax = bb, rr_true = bb, beta = 0.0;
+  int it = 0, flags = 0, updates = 0;
+  bool done = !(bb > 0.0) || !isfinite(bb);
+  if (!isfinite(bb)) flags |= 2;
+
+  while (!done) {
+    // p <- r + beta p on the thread's own sites
+    const float fb = (float)beta;
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) {
+      const int l = threadIdx.x + k * blockDim.x;
+      if (l < V) ps[l] = f4_of(r[k] + fb * sp_of(ps[l]));
+    }
+    __syncthreads();
+    // t = D p and p^dag A p = |t|^2
+    double pap = 0.0;
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) {
+      const int l = threadIdx.x + k * blockDim.x;
+      if (l < V) {
+        const Sp<float> tv = dslash_smem<false>(ps, Us, neighbours(l, ci.L, ci.T, lshift), diag);
+        ts[l] = f4_of(tv);
+        pap += (double)norm2(tv);
+      }
+    }
+    pap = cta_sum(pap, red);  // its barriers also publish ts
+    if (!(pap > 0.0) || !isfinite(pap)) {
+      flags |= 2;
+      break;
+    }
+    const float alpha = (float)(rr / pap);
+    // A p = D^dag t; x += alpha p; r -= alpha A p
+    double rn = 0.0;
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) {
+      const int l = threadIdx.x + k * blockDim.x;
+      if (l < V) {
+        const Sp<float> Ap = dslash_smem<true>(ts, Us, neighbours(l, ci.L, ci.T, lshift), diag);
+        x[k] = x[k] + alpha * sp_of(ps[l]);
+        r[k] = r[k] - alpha * Ap;
+        rn += (double)norm2(r[k]);
+      }
+    }
+    rn = cta_sum(rn, red);
+    rr_prev = rr;
+    rr = rn;
+    beta = rr / rr_prev;
+    ++it;
+    if (!isfinite(rr)) {
+      flags |= 2;
+      break;
+    }
+    rmax = fmax(rmax, rr);
+    const bool conv = rr <= a.tol2 * bb;
+    if (conv || rr < a.delta2 * rmax || it >= a.maxit) {
+      // reliable update: x_hi += x, r = b - A x_hi in FP64
+#pragma unroll
+      for (int k = 0; k < SPT; ++k) {
+        const int l = threadIdx.x + k * blockDim.x;
+        if (l < V) {
+          st_sp(a.x, ci.off + l, ld_sp_cg(a.x, ci.off + l) + to_dbl(x[k]));
+          x[k] = {{0.f, 0.f}, {0.f, 0.f}};
+        }
+      }
+      __syncthreads();
+      rr_true = true_residual(a, ci, lshift, red, [&](int k, int, const Sp<double>& rv) {
+#pragma unroll
+        for (int j = 0; j < SPT; ++j)
+          if (j == k) r[j] = to_flt(rv);
+      });
+      ++updates;
+      if (!isfinite(rr_true)) {
+        flags |= 2;
+        break;
+      }
+      if (rr_true <= a.tol2 * bb) break;
+      if (it >= a.maxit) {
+        flags |= 1;
+        break;
+      }
+      beta = rr_true / rr_prev;
+      rr = rr_true;
+      rmax = rr_true;
+    }
+  }
+  if (threadIdx.x == 0) {
+    cc->bb = bb;
+    cc->rr = rr;
+    cc->rr_true = rr_true;
+    cc->iters = it;
+    cc->flags = flags;
+    cc->state = 0;
+    cc->need_update = updates;  // reports the number of reliable updates
+  }
+}
+
+// FP64: the same iteration with all fields in global memory (x is the output,
+// r64, p64, t64 scratch), one block per chain.
+__global__ void __launch_bounds__(kChainThreads, 1) k_cg_chain_f64(ChainCgArgs a) {
+  __shared__ double red[33];
+  const int c = a.list[blockIdx.x];
+  const ChainInfo ci = a.chains[c];
+  CgChain* cc = a.cgc + c;
+  const int V = ci.L * ci.T;
+  const long long off = ci.off;
+  const int lshift = (ci.L & (ci.L - 1)) == 0 ? __ffs(ci.L) - 1 : -1;
+  const double diag = 2.0 + ci.m0;
+  const Sp<double> z = {{0, 0}, {0, 0}};
+  double bb = 0.0;
+  for (int l = threadIdx.x; l < V; l += blockDim.x) {
+    const Sp<double> bv = ld_sp(a.b, off + l);
+    bb += norm2(bv);
+    st_sp(a.r64, off + l, bv);
+    st_sp(a.p64, off + l, z);
+    st_sp(a.x, off + l, z);
+  }
+  bb = cta_sum(bb, red);
+  double rr = bb, beta = 0.0;
+  int it = 0, flags = 0;
+  bool done = !(bb > 0.0) || !isfinite(bb);
+  if (!isfinite(bb)) flags |= 2;
+  while (!done) {
+    for (int l = threadIdx.x; l < V; l += blockDim.x)
+      st_sp(a.p64, off + l, ld_sp_cg(a.r64, off + l) + beta * ld_sp_cg(a.p64, off + l));
+    __syncthreads();
+    double pap = 0.0;
+    for (int l = threadIdx.x; l < V; l += blockDim.x) {
+      const Sp<double> tv =
+          dslash_glob<false>(a.p64, a.U64, off, neighbours(l, ci.L, ci.T, lshift), diag);
+      st_sp(a.t64, off + l, tv);
+      pap += norm2(tv);
+    }
+    pap = cta_sum(pap, red);
+    if (!(pap > 0.0) || !isfinite(pap)) {
+      flags |= 2;
+      break;
+    }
+    const double alpha = rr / pap;
+    double rn = 0.0;
+    for (int l = threadIdx.x; l < V; l += blockDim.x) {
+      const Sp<double> Ap =
+          dslash_glob<true>(a.t64, a.U64, off, neighbours(l, ci.L, ci.T, lshift), diag);
+      st_sp(a.x, off + l, ld_sp_cg(a.x, off + l) + alpha * ld_sp_cg(a.p64, off + l));
+      const Sp<double> rv = ld_sp_cg(a.r64, off + l) - alpha * Ap;
+      st_sp(a.r64, off + l, rv);
+      rn += norm2(rv);
+    }
+    rn = cta_sum(rn, red);
+    beta = rn / rr;
+    rr = rn;
+    ++it;
+    if (!isfinite(rr)) {
+      flags |= 2;
+      break;
+    }
+    if (rr <= a.tol2 * bb) break;
+    if (it >= a.maxit) {
+      flags |= 1;
+      break;
+    }
+  }
+  __syncthreads();
+  // report the FP64 true residual of the result
+  const double rt = true_residual(a, ci, lshift, red, [](int, int, const Sp<double>&) {});
+  if (threadIdx.x == 0) {
+    cc->bb = bb;
+    cc->rr = rr;
+    cc->rr_true = rt;
+    cc->iters = it;
+    cc->flags = flags;
+    cc->state = 0;
+    cc->need_update = 0;
+  }
+}
+
+// Largest chain volume the shared-memory FP32 form holds (48 B per site).
+constexpr int kChainMaxVolume = 4096;
+
+bool chain_cg_fits(const sm_lattice* L, int prec) {
+  int vmax = 0;
+  for (const ChainInfo& ci : L->chains) vmax = ci.L * ci.T > vmax ? ci.L * ci.T : vmax;
+  if (prec == SM_MIXED) return vmax <= kChainMaxVolume;
+  return vmax <= 4 * kChainMaxVolume;
+}
+
+int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
+                    const sm_cg_params& cg) {
+  const sm_lattice* L = c.L;
+  ChainCgArgs a{};
+  a.chains = L->d_chains;
+  a.list = L->d_chain_list;
+  a.U32 = U32;
+  a.U64 = U64;
+  a.b = b;
+  a.x = x;
+  a.t64 = c.w.t;
+  a.r64 = c.w.r;
+  a.p64 = c.w.p0;
+  a.cgc = c.w.cgc;
+  a.tol2 = cg.tol * cg.tol;
+  a.delta2 = cg.delta * cg.delta;
+  a.maxit = cg.maxit;
+  const dim3 grid((unsigned)L->nchains), block(kChainThreads);
+  if (cg.prec == SM_MIXED) {
+    int vmax = 0;
+    for (const ChainInfo& ci : L->chains) vmax = ci.L * ci.T > vmax ? ci.L * ci.T : vmax;
+    const size_t smem = (size_t)3 * vmax * sizeof(float4);
+    const int spt = (vmax + kChainThreads - 1) / kChainThreads;
+    cudaError_t e = cudaSuccess;
+    if (spt <= 1) {
+      e = cudaFuncSetAttribute(k_cg_chain_mixed<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) k_cg_chain_mixed<1><<<grid, block, smem, c.s>>>(a);
+    } else if (spt <= 2) {
+      e = cudaFuncSetAttribute(k_cg_chain_mixed<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) k_cg_chain_mixed<2><<<grid, block, smem, c.s>>>(a);
+    } else {
+      e = cudaFuncSetAttribute(k_cg_chain_mixed<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) k_cg_chain_mixed<4><<<grid, block, smem, c.s>>>(a);
+    }
+    if (e != cudaSuccess) return fail(SM_ERR_CUDA, "chain CG attribute: %s", cudaGetErrorString(e));
+    return launched(c.st, "cg_chain_mixed");
+  }
+  k_cg_chain_f64<<<grid, block, 0, c.s>>>(a);
+  return launched(c.st, "cg_chain_f64");
+}
+
+}  // namespace sm

@@ -541,6 +541,12 @@ int sm_lattice_create(int nchains, const int* L, const int* T, const double* bet
   cudaGetDevice(&lat->device);
   cudaError_t e = cudaMalloc(&lat->d_chains, sizeof(ChainInfo) * nchains);
   if (e == cudaSuccess) e = cudaMalloc(&lat->d_blk_chain, sizeof(int) * blk);
+  if (e == cudaSuccess) e = cudaMalloc(&lat->d_chain_list, sizeof(int) * nchains);
+  if (e == cudaSuccess) {
+    std::vector<int> ids(nchains);
+    for (int i = 0; i < nchains; ++i) ids[i] = i;
+    e = cudaMemcpy(lat->d_chain_list, ids.data(), sizeof(int) * nchains, cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess)
     e = cudaMemcpy(lat->d_chains, lat->chains.data(), sizeof(ChainInfo) * nchains,
                    cudaMemcpyHostToDevice);
@@ -561,6 +567,7 @@ int sm_lattice_destroy(sm_lattice* lat) {
   if (!lat) return SM_OK;
   if (lat->d_chains) cudaFree(lat->d_chains);
   if (lat->d_blk_chain) cudaFree(lat->d_blk_chain);
+  if (lat->d_chain_list) cudaFree(lat->d_chain_list);
   if (lat->h_pinned) cudaFreeHost(lat->h_pinned);
   if (lat->ev[0]) cudaEventDestroy(lat->ev[0]);
   if (lat->ev[1]) cudaEventDestroy(lat->ev[1]);

@@ -17,6 +17,7 @@ struct sm_lattice {
   std::vector<sm::ChainInfo> chains;
   sm::ChainInfo* d_chains;
   int* d_blk_chain;
+  int* d_chain_list;  // [nchains] 0, 1, ..., nchains - 1
   int device;
   int* h_pinned;  // small pinned host buffer for per-call readbacks
   cudaEvent_t ev[2];  // readback events of the CG loop
@@ -112,6 +113,11 @@ int launch_lincomb(Ctx& c, double* y, const double* w, double a, const double* x
 int launch_energies(Ctx& c, const double* q, const double* p, const double* phi, const double* xi,
                     double* K, double* SG, double* SF);
 int launch_copy_links_masked(Ctx& c, double* dst, const double* src, const int* mask);
+
+// Chain-resident CG (cg_chain.cu): one block per chain.
+bool chain_cg_fits(const sm_lattice* L, int prec);
+int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
+                    const sm_cg_params& cg);
 
 // CG on D^dag D (solver.cu).  b, x FP64; x is overwritten.  If iters/relres
 // are non-NULL they receive host copies.  Synchronises.

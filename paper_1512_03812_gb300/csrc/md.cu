@@ -300,7 +300,7 @@ int sm_force(const sm_lattice* lat, const double* q, const double* phi, int part
     SM_TRY(fields_ok({phi}, "sm_force"));
     SM_TRY(make_links(c, q, c.w.U64, c.w.U32, *cg));
   }
-  sm_cg_params dummy{1e-10, 1, SM_F64, 0.1};
+  sm_cg_params dummy{1e-10, 1, SM_F64, 0.1, SM_CG_AUTO};
   SM_TRY(force_at(c, q, c.w.U64, c.w.U32, phi, part, cg ? *cg : dummy, F, nullptr, 0.0));
   return c.sync();
 }

@@ -392,11 +392,23 @@ int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, doubl
   af.maxit = cg.maxit;
   af.mixed = mixed ? 1 : 0;
 
+  if (cg.algo < SM_CG_AUTO || cg.algo > SM_CG_CHAIN) return fail(SM_ERR_ARG, "cg_solve: bad algo");
+  const bool fits = chain_cg_fits(c.L, cg.prec);
+  if (cg.algo == SM_CG_CHAIN && !fits)
+    return fail(SM_ERR_ARG, "cg_solve: a chain is too large for the chain-resident solver");
+  const bool chain = cg.algo == SM_CG_CHAIN || (cg.algo == SM_CG_AUTO && fits);
+
   SM_CU(cudaMemsetAsync(c.w.n_active, 0, sizeof(int), c.s));
   long long batched = 0, updates = 0;
   int rc;
   const int chunk = 8;
-  if (mixed) {
+  if (chain) {
+    if ((rc = prof_record(g_prof.e0, 0, c.s))) return rc;
+    if ((rc = chain_cg_launch(c, U64, U32, b, x, cg))) return rc;
+    if ((rc = prof_record(g_prof.e1, 0, c.s))) return rc;
+    SM_CU(cudaStreamSynchronize(c.s));
+    if ((rc = prof_collect(0, false))) return rc;
+  } else if (mixed) {
     k_cg_init<float><<<c.grid(), kBlock, 0, c.s>>>(c.g, af);
     if ((rc = launched(c.st, "cg_init"))) return rc;
     if ((rc = run<float>(c, af, af, chunk, cg.maxit, &batched, &updates))) return rc;
@@ -437,6 +449,16 @@ int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, doubl
       g_prof.site_iters += (long long)h[i].iters * c.L->chains[i].L * c.L->chains[i].T;
   }
   c.st->reliable_updates += updates;
+  if (chain) {
+    int mx = 0;
+    for (const CgChain& ch : h) {
+      mx = ch.iters > mx ? ch.iters : mx;
+      updates += ch.need_update;
+    }
+    batched = mx;
+    c.st->reliable_updates += updates;
+    updates = 0;
+  }
   int worst = SM_OK;
   if (!c.strict && c.chain_flags.size() != h.size()) c.chain_flags.assign(h.size(), 0);
   for (int i = 0; i < c.L->nchains; ++i) {

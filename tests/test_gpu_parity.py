@@ -33,9 +33,9 @@ def torch():
     return t
 
 
-def cg(tol=1e-14, prec="f64", maxit=20000):
+def cg(tol=1e-14, prec="f64", maxit=20000, algo="auto"):
     import paper_1512_03812_gb300 as P
-    return P.CG(tol=tol, maxit=maxit, prec=prec)
+    return P.CG(tol=tol, maxit=maxit, prec=prec, algo=algo)
 
 
 def batch(torch, dims=DIMS, seed=0, betas=(2.0, 1.0, 4.0, 2.0, 1.5, 3.0), kappas=(0.24, 0.2, 0.22, 0.25, 0.21, 0.23)):
@@ -79,11 +79,12 @@ def test_apply_DdagD(torch):
         assert rel_err(b.chain(out32, c), ref) < 4e-6
 
 
-def test_cg_f64_matches_oracle(torch):
+@pytest.mark.parametrize("algo", ["grid", "chain"])
+def test_cg_f64_matches_oracle(torch, algo):
     b = batch(torch)
     q, phi = b.q(), b.spinor()
     U64, U32 = b.lat.links(b.dev(q))
-    x, iters, relres = b.lat.cg_solve(U64, U32, b.dev(phi), cg(1e-14))
+    x, iters, relres = b.lat.cg_solve(U64, U32, b.dev(phi), cg(1e-14, algo=algo))
     assert (relres < 1e-13).all(), relres
     for c, ol in enumerate(b.olat):
         ref = sw.Solver(tol=1e-14).cg(ol, sw.links(b.chain(q, c)), b.chain(phi, c))
@@ -91,12 +92,16 @@ def test_cg_f64_matches_oracle(torch):
         assert iters[c] > 0
 
 
-def test_cg_mixed_reaches_fp64_true_residual(torch):
+@pytest.mark.parametrize("algo", ["grid", "chain"])
+@pytest.mark.parametrize("delta", [0.1, 0.01])
+def test_cg_mixed_reaches_fp64_true_residual(torch, algo, delta):
+    import paper_1512_03812_gb300 as P
     b = batch(torch)
     q, phi = b.q(), b.spinor()
     U64, U32 = b.lat.links(b.dev(q))
     x64, _, _ = b.lat.cg_solve(U64, U32, b.dev(phi), cg(1e-12))
-    xm, iters, relres = b.lat.cg_solve(U64, U32, b.dev(phi), cg(1e-10, "mixed"))
+    xm, iters, relres = b.lat.cg_solve(U64, U32, b.dev(phi),
+                                       P.CG(tol=1e-10, prec="mixed", delta=delta, algo=algo))
     assert (relres <= 1e-10).all(), relres
     # an independent check of the residual with the FP64 operator
     r = b.dev(phi) - b.lat.apply_DdagD(U64, xm)
@@ -106,17 +111,38 @@ def test_cg_mixed_reaches_fp64_true_residual(torch):
         assert rel_err(b.chain(xm, c), b.chain(x64, c)) < 1e-8
 
 
-def test_cg_zero_rhs_and_maxit(torch):
+@pytest.mark.parametrize("algo", ["grid", "chain"])
+def test_cg_zero_rhs_and_maxit(torch, algo):
     import paper_1512_03812_gb300 as P
     b = batch(torch, dims=[(8, 8), (4, 4)])
     U64, U32 = b.lat.links(b.dev(b.q()))
     zero = torch.zeros((b.lat.N, 2), dtype=torch.complex128, device="cuda")
-    x, iters, relres = b.lat.cg_solve(U64, U32, zero, cg(1e-10))
-    assert (iters == 0).all() and float(x.abs().max()) == 0.0
-    with pytest.raises(P.NotConverged):
-        b.lat.cg_solve(U64, U32, b.dev(b.spinor()), cg(1e-14, maxit=3))
-    with pytest.raises(P.NotConverged):
-        b.lat.cg_solve(U64, U32, b.dev(b.spinor()), cg(1e-14, "mixed", maxit=3))
+    for prec in ("f64", "mixed"):
+        x, iters, relres = b.lat.cg_solve(U64, U32, zero, cg(1e-10, prec, algo=algo))
+        assert (iters == 0).all() and float(x.abs().max()) == 0.0
+        with pytest.raises(P.NotConverged):
+            b.lat.cg_solve(U64, U32, b.dev(b.spinor()), cg(1e-14, prec, maxit=3, algo=algo))
+
+
+def test_cg_layouts_agree(torch):
+    """Grid-wide and chain-resident solves of the same batch agree (FP64 to
+    rounding; mixed both meet the FP64 true-residual tolerance)."""
+    b = batch(torch)
+    q, phi = b.q(), b.spinor()
+    U64, U32 = b.lat.links(b.dev(q))
+    xg, ig_, _ = b.lat.cg_solve(U64, U32, b.dev(phi), cg(1e-13, algo="grid"))
+    xc, ic_, _ = b.lat.cg_solve(U64, U32, b.dev(phi), cg(1e-13, algo="chain"))
+    assert (np.abs(ig_ - ic_) <= 1).all()
+    for c in range(len(b.dims)):
+        assert rel_err(b.chain(xg, c), b.chain(xc, c)) < 1e-12
+
+
+def test_chain_solver_rejects_oversized_chains(torch):
+    import paper_1512_03812_gb300 as P
+    b = batch(torch, dims=[(128, 64)])
+    U64, U32 = b.lat.links(b.dev(b.q()))
+    with pytest.raises(P.SchwingerError):
+        b.lat.cg_solve(U64, U32, b.dev(b.spinor()), cg(1e-10, "mixed", algo="chain"))
 
 
 def test_forces(torch):
@@ -241,7 +267,8 @@ def test_md_trajectory(torch, scheme, M, fg, merge):
                                          ("nested_five_stage", 2, "exact"),
                                          ("adapted_nested_fg", 2, "exact"),
                                          ("adapted_nested_fg", 2, "shifted")])
-def test_hmc_trajectory_parity(torch, scheme, M, fg):
+@pytest.mark.parametrize("algo", ["grid", "chain"])
+def test_hmc_trajectory_parity(torch, scheme, M, fg, algo):
     """8x8, beta 2, kappa 0.24: Delta H to 1e-12 relative to H and identical
     Metropolis decisions, over chains started from seeded hot links."""
     import paper_1512_03812_gb300 as P
@@ -250,7 +277,7 @@ def test_hmc_trajectory_parity(torch, scheme, M, fg):
     q, p, eta = b.q(), b.p(), b.eta()
     us = np.linspace(0.05, 0.95, n_ch)
     qd = b.dev(q)
-    md = P.MD(scheme=scheme, tau=1.0, n=5, M=M, fg=fg, cg=cg(1e-14))
+    md = P.MD(scheme=scheme, tau=1.0, n=5, M=M, fg=fg, cg=cg(1e-14, algo=algo))
     q_md = torch.empty_like(qd)
     dH, H0, acc = b.lat.hmc_trajectory(qd, b.dev(p), b.dev(eta), us, md, q_md=q_md)
     for c, ol in enumerate(b.olat):
