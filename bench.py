@@ -34,14 +34,41 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = {
     "workload": "64x64 beta=2.0 kappa=0.26, 200 chains/GPU, adapted nested FG n=8 m=2, "
-                "mixed-precision CG tol 1e-10",
+                "mixed-precision CG tol 1e-10 (1e-12 for the S_F of H)",
     "L": 64, "T": 64, "beta": 2.0, "kappa": 0.26, "chains_per_gpu": 200,
     "scheme": "adapted_nested_fg", "tau": 1.0, "n": 8, "M": 2, "fg": "exact",
-    "cg_tol": 1e-10, "precision": "mixed",
+    "cg_tol": 1e-10, "cg_tol_action": 1e-12, "cg_delta": 0.01, "precision": "mixed",
 }
-# algorithmic bytes per site and CG iteration of the FP32 iteration pair
-# (kernel A: r, p, U in, p, t out; kernel B: t, U, p, x, r in, x, r out; 16 B each)
+# Global-memory bytes per site and CG iteration of a memory-resident CG
+# iteration (the grid-wide pair of solver.cu: kernel A reads r, p, U and
+# writes p, t; kernel B reads t, U, p, x, r and writes x, r; 16 B each in
+# FP32, 32 B in FP64).
 CG_BYTES_PER_SITE_ITER = {"mixed": (3 + 2) * 16 + (5 + 2) * 16, "f64": (3 + 2) * 32 + (5 + 2) * 32}
+# Shared-memory bytes per site and iteration of the chain-resident FP32 CG
+# (cg_chain.cu): p update 2 x 16, t = D p reads 5 p + 3 U and writes t
+# (9 x 16), D^dag t reads 5 t + 3 U + p (9 x 16).
+SMEM_BYTES_PER_SITE_ITER = 20 * 16
+# Shared-memory bandwidth per SM and clock (32 banks x 4 B).
+SMEM_BYTES_PER_CLK_PER_SM = 128
+NUM_SMS = 152
+# DRAM traffic of one launch of the chain-resident kernel from the ncu
+# capture in profiles/cg_chain_mixed_64x64x200.md; reported only while the
+# kernel source is unchanged since the capture.
+NCU_TRAFFIC = {"kernel": "k_cg_chain_mixed<8,512>",
+               "sources": {"paper_1512_03812_gb300/csrc/cg_chain.cu": "1571bd342ed6a2b9",
+                           "paper_1512_03812_gb300/csrc/common.cuh": "df919ebc12c4bab8"},
+               "dram_bytes_per_launch": 276316416 + 333173504}
+
+
+def _sha16(path):
+    import hashlib
+    with open(os.path.join(ROOT, path), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic():
+    ok = all(_sha16(p) == h for p, h in NCU_TRAFFIC["sources"].items())
+    return NCU_TRAFFIC["dram_bytes_per_launch"] if ok else None
 
 
 def kappa_to_m0(k):
@@ -161,9 +188,10 @@ def run_ours(args):
     m0 = kappa_to_m0(W["kappa"])
     lat = P.Lattice([L] * B, [T] * B, W["beta"], m0, device=dev)
     N = lat.N
-    W = dict(W, n=args.n, M=args.M)
+    W = dict(W, n=args.n, M=args.M, cg_delta=args.delta)
     cgp = P.CG(tol=W["cg_tol"], maxit=20000, prec=args.prec, delta=args.delta, algo=args.algo)
-    md = P.MD(scheme=W["scheme"], tau=W["tau"], n=W["n"], M=W["M"], fg=W["fg"], cg=cgp)
+    md = P.MD(scheme=W["scheme"], tau=W["tau"], n=W["n"], M=W["M"], fg=W["fg"], cg=cgp,
+              tol_action=W["cg_tol_action"])
     gen = torch.Generator(device=dev)
     gen.manual_seed(shard(world, rank, B)["seed"])
 
@@ -186,9 +214,9 @@ def run_ours(args):
     fine = P.CG(1e-8, 20000, "mixed")
     phases = [(0.10, P.MD(scheme="nested_leapfrog", tau=1.0, n=5, M=8, cg=fine), args.therm, 0.0),
               (W["kappa"], P.MD(scheme="nested_leapfrog", tau=1.0, n=16, M=4, cg=fine),
-               max(2, args.therm // 2), 0.0),
+               args.therm // 2, 0.0),
               (W["kappa"], P.MD(scheme="nested_leapfrog", tau=1.0, n=16, M=4, cg=fine),
-               max(2, args.therm // 4), None)]
+               args.therm // 4, None)]
     for kap, mdt, ntraj, uforce in phases:
         one = P.Lattice(L, T, W["beta"], kappa_to_m0(kap), device=dev)
         for _ in range(ntraj):
@@ -274,11 +302,12 @@ def run_ours(args):
     fp64 = None
     if args.fp64_steps > 0:
         md64 = P.MD(scheme=W["scheme"], tau=W["tau"], n=W["n"], M=W["M"], fg=W["fg"],
-                    cg=P.CG(tol=W["cg_tol"], maxit=20000, prec="f64", algo=args.algo))
+                    cg=P.CG(tol=W["cg_tol"], maxit=20000, prec="f64", algo=args.algo),
+                    tol_action=W["cg_tol_action"])
         q64 = q_start.clone()
         qm = q_start.clone()
         dev_max = 0.0
-        acc64 = []
+        acc64, accm = [], []
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
@@ -290,28 +319,47 @@ def run_ours(args):
             f1.record()
             torch.cuda.synchronize()
             t64 += f0.elapsed_time(f1)
-            dm, _, _ = lat.hmc_trajectory(qm, pk[i], ek[i], uk[i], md, check=False)
+            dm, _, am = lat.hmc_trajectory(qm, pk[i], ek[i], uk[i], md, check=False)
+            accm.append(am)
             ok = np.isfinite(d64) & np.isfinite(dm)
             dev_max = max(dev_max, float(np.abs(d64[ok] - dm[ok]).max()) if ok.any() else 0.0)
             acc64.append(a64)
             qm.copy_(q64)
         fp64 = {"traj_per_s": world * B * args.fp64_steps / (t64 / 1e3),
                 "acc": float(np.mean(np.concatenate(acc64))),
+                "acc_mixed_same_inputs": float(np.mean(np.concatenate(accm))),
                 "max_abs_dH_mixed_minus_fp64": dev_max, "steps": args.fp64_steps}
 
-    # roofline of the dominant kernels (the CG iteration pair)
+    # roofline of the dominant kernel: the CG solve.  The chain-resident form
+    # (every chain of this workload fits) keeps U, p, t in shared memory and
+    # x, r in registers, so its bound is shared-memory bandwidth, not HBM.
     peaks, src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
     bps = CG_BYTES_PER_SITE_ITER[args.prec]
-    achieved = bps * prof["site_iters"] / (prof["iter_ms"] / 1e3) / 1e9 if prof["iter_ms"] else 0
-    peak = float(peaks["hbm_gbs"])
-    roofline = {"bound": "hbm", "kernel": "cg iteration (k_cg_a + k_cg_b)",
-                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": src,
-                "traffic": None,
-                "bytes_per_site_iter": bps, "site_iters": prof["site_iters"],
-                "kernel_ms": round(prof["iter_ms"], 3),
-                "kernel_share_of_step": round(prof["iter_ms"] / ms, 4),
-                "res_ms": round(prof["res_ms"], 3)}
+    ksec = prof["iter_ms"] / 1e3
+    hbm_eq = bps * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
+    chain = args.algo == "chain" or (args.algo == "auto" and args.prec == "mixed")
+    if chain and args.prec == "mixed":
+        f_mhz = (clk or {}).get("sm_mhz") or 2070.0
+        peak = NUM_SMS * SMEM_BYTES_PER_CLK_PER_SM * f_mhz * 1e6 / 1e9
+        ach = SMEM_BYTES_PER_SITE_ITER * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
+        roofline = {"bound": "smem", "kernel": "k_cg_chain_mixed (chain-resident CG)",
+                    "achieved": round(ach, 1), "peak": round(peak, 1), "unit": "GB/s",
+                    "frac": round(ach / peak, 4),
+                    "peak_source": f"{NUM_SMS} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x "
+                                   f"{f_mhz:.0f} MHz (median SM clock under load)",
+                    "bytes_per_site_iter": SMEM_BYTES_PER_SITE_ITER,
+                    "traffic": ncu_traffic(), "traffic_unit": "DRAM bytes per launch (ncu)",
+                    "hbm_equivalent": {"achieved": round(hbm_eq, 1), "peak": hbm,
+                                       "unit": "GB/s", "frac": round(hbm_eq / hbm, 4),
+                                       "bytes_per_site_iter": bps, "peak_source": src}}
+    else:
+        roofline = {"bound": "hbm", "kernel": "cg iteration (k_cg_a + k_cg_b)",
+                    "achieved": round(hbm_eq, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(hbm_eq / hbm, 4), "peak_source": src, "traffic": None,
+                    "bytes_per_site_iter": bps}
+    roofline.update({"site_iters": prof["site_iters"], "kernel_ms": round(prof["iter_ms"], 3),
+                     "kernel_share_of_step": round(prof["iter_ms"] / ms, 4)})
 
     if rank != 0:
         return
@@ -394,7 +442,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])
     ap.add_argument("--M", type=int, default=WORKLOAD["M"])
-    ap.add_argument("--delta", type=float, default=0.1)
+    ap.add_argument("--delta", type=float, default=0.01)
     ap.add_argument("--algo", default="auto", choices=["auto", "grid", "chain"])
     args = ap.parse_args()
     if args.impl == "reference":

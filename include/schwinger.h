@@ -124,6 +124,8 @@ typedef struct {
   int fg;
   int merge_kicks;
   sm_cg_params cg;
+  double tol_action;  /* CG tolerance of the S_F solves of H in sm_hmc_trajectory
+                         (0: cg.tol); the MD force solves use cg.tol */
 } sm_md_params;
 
 /* Counters accumulated over one call (zeroed by the call). */

@@ -58,7 +58,7 @@ class CgParams(ctypes.Structure):
 class MdParams(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int), ("tau", ctypes.c_double), ("n", ctypes.c_int),
                 ("M", ctypes.c_int), ("lambda_", ctypes.c_double), ("fg", ctypes.c_int),
-                ("merge_kicks", ctypes.c_int), ("cg", CgParams)]
+                ("merge_kicks", ctypes.c_int), ("cg", CgParams), ("tol_action", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -181,12 +181,13 @@ class MD:
     fg: str = "exact"       # "exact" or "shifted"
     merge_kicks: bool = True
     cg: CG = None
+    tol_action: float = 0.0  # tolerance of the S_F solves of H (0: cg.tol)
 
     def c(self) -> MdParams:
         cg = self.cg or CG()
         return MdParams(SCHEMES[self.scheme], self.tau, self.n, self.M, self.lam,
                         {"exact": FG_EXACT, "shifted": FG_SHIFTED}[self.fg],
-                        1 if self.merge_kicks else 0, cg.c())
+                        1 if self.merge_kicks else 0, cg.c(), self.tol_action)
 
 
 class Lattice:

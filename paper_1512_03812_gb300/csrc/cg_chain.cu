@@ -37,7 +37,7 @@ struct ChainCgArgs {
   int maxit;
 };
 
-// Sum over the block, returned to every thread.
+// Sum over the block, returned to every thread (FP64 partials).
 __device__ __forceinline__ double cta_sum(double v, double* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -54,6 +54,27 @@ __device__ __forceinline__ double cta_sum(double v, double* red) {
   }
   __syncthreads();
   return red[32];
+}
+
+// Block reduction of FP32 per-thread partials: warps add in FP32, the 32
+// warp sums are added in FP64 by warp 0, and thread 0 receives the total in
+// `fin(total)`, which may update shared scalars.  Ends with a barrier, so
+// whatever `fin` wrote is visible to every thread on return.  On GB300 the
+// FP64 pipe is a small fraction of the FP32 one: only warp 0 touches it.
+template <typename Fin>
+__device__ __forceinline__ void cta_reduce(float v, double* red, Fin fin) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) red[w] = (double)v;
+  __syncthreads();
+  if (w == 0) {
+    double s = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) fin(s);
+  }
+  __syncthreads();
 }
 
 // Coordinates and neighbours of local site l of an L x T chain.
@@ -140,15 +161,24 @@ __device__ __forceinline__ double true_residual(const ChainCgArgs& a, const Chai
   return cta_sum(v, red);
 }
 
+// Scalars of a chain-resident solve, owned by thread 0 and broadcast
+// through shared memory.
+struct ChainScalars {
+  double bb, rr, rr_prev, rmax, rr_true;
+  float alpha, beta;
+  int it, flags, updates;
+  int action;  // 0 iterate, 1 reliable update, 2 stop
+};
+
 // Mixed precision: FP32 iterations in shared memory and registers, FP64
 // reliable updates.  SPT sites per thread (V <= SPT * blockDim.x).
-template <int SPT>
-__global__ void __launch_bounds__(kChainThreads, 1) k_cg_chain_mixed(ChainCgArgs a) {
+template <int SPT, int NT>
+__global__ void __launch_bounds__(NT, 1) k_cg_chain_mixed(ChainCgArgs a) {
   extern __shared__ float4 smem[];
   __shared__ double red[33];
+  __shared__ ChainScalars S;
   const int c = a.list[blockIdx.x];
   const ChainInfo ci = a.chains[c];
-  CgChain* cc = a.cgc + c;
   const int V = ci.L * ci.T;
   const int lshift = (ci.L & (ci.L - 1)) == 0 ? __ffs(ci.L) - 1 : -1;
   float4* Us = smem;
@@ -157,7 +187,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_cg_chain_mixed(ChainCgArgs
   const float diag = (float)(2.0 + ci.m0);
 
   Sp<float> x[SPT], r[SPT];
-  double bb = 0.0;
+  double bbl = 0.0;
 #pragma unroll
   for (int k = 0; k < SPT; ++k) {
     const int l = threadIdx.x + k * blockDim.x;
@@ -166,21 +196,26 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_cg_chain_mixed(ChainCgArgs
     if (l < V) {
       Us[l] = __ldg(reinterpret_cast<const float4*>(a.U32) + ci.off + l);
       const Sp<double> bv = ld_sp(a.b, ci.off + l);
-      bb += norm2(bv);
+      bbl += norm2(bv);
       r[k] = to_flt(bv);
       ps[l] = make_float4(0.f, 0.f, 0.f, 0.f);
       st_sp(a.x, ci.off + l, Sp<double>{{0, 0}, {0, 0}});
     }
   }
-  bb = cta_sum(bb, red);
-  double rr = bb, rr_prev = bb, rmax = bb, rr_true = bb, beta = 0.0;
-  int it = 0, flags = 0, updates = 0;
-  bool done = !(bb > 0.0) || !isfinite(bb);
-  if (!isfinite(bb)) flags |= 2;
+  const double bb = cta_sum(bbl, red);
+  if (threadIdx.x == 0) {
+    S.bb = bb;
+    S.rr = S.rr_prev = S.rmax = S.rr_true = bb;
+    S.beta = 0.f;
+    S.it = S.updates = 0;
+    S.flags = isfinite(bb) ? 0 : 2;
+    S.action = (bb > 0.0 && isfinite(bb)) ? 0 : 2;
+  }
+  __syncthreads();
 
-  while (!done) {
+  while (S.action != 2) {
     // p <- r + beta p on the thread's own sites
-    const float fb = (float)beta;
+    const float fb = S.beta;
 #pragma unroll
     for (int k = 0; k < SPT; ++k) {
       const int l = threadIdx.x + k * blockDim.x;
@@ -188,24 +223,28 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_cg_chain_mixed(ChainCgArgs
     }
     __syncthreads();
     // t = D p and p^dag A p = |t|^2
-    double pap = 0.0;
+    float pap = 0.f;
 #pragma unroll
     for (int k = 0; k < SPT; ++k) {
       const int l = threadIdx.x + k * blockDim.x;
       if (l < V) {
         const Sp<float> tv = dslash_smem<false>(ps, Us, neighbours(l, ci.L, ci.T, lshift), diag);
         ts[l] = f4_of(tv);
-        pap += (double)norm2(tv);
+        pap += norm2(tv);
       }
     }
-    pap = cta_sum(pap, red);  // its barriers also publish ts
-    if (!(pap > 0.0) || !isfinite(pap)) {
-      flags |= 2;
-      break;
-    }
-    const float alpha = (float)(rr / pap);
+    cta_reduce(pap, red, [&](double s) {  // its barriers also publish ts
+      if (s > 0.0 && isfinite(s)) {
+        S.alpha = (float)(S.rr / s);
+      } else {
+        S.flags |= 2;
+        S.action = 2;
+      }
+    });
+    if (S.action == 2) break;
+    const float alpha = S.alpha;
     // A p = D^dag t; x += alpha p; r -= alpha A p
-    double rn = 0.0;
+    float rn = 0.f;
 #pragma unroll
     for (int k = 0; k < SPT; ++k) {
       const int l = threadIdx.x + k * blockDim.x;
@@ -213,21 +252,24 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_cg_chain_mixed(ChainCgArgs
         const Sp<float> Ap = dslash_smem<true>(ts, Us, neighbours(l, ci.L, ci.T, lshift), diag);
         x[k] = x[k] + alpha * sp_of(ps[l]);
         r[k] = r[k] - alpha * Ap;
-        rn += (double)norm2(r[k]);
+        rn += norm2(r[k]);
       }
     }
-    rn = cta_sum(rn, red);
-    rr_prev = rr;
-    rr = rn;
-    beta = rr / rr_prev;
-    ++it;
-    if (!isfinite(rr)) {
-      flags |= 2;
-      break;
-    }
-    rmax = fmax(rmax, rr);
-    const bool conv = rr <= a.tol2 * bb;
-    if (conv || rr < a.delta2 * rmax || it >= a.maxit) {
+    cta_reduce(rn, red, [&](double s) {
+      S.rr_prev = S.rr;
+      S.rr = s;
+      S.beta = (float)(s / S.rr_prev);
+      S.it += 1;
+      if (!isfinite(s)) {
+        S.flags |= 2;
+        S.action = 2;
+        return;
+      }
+      S.rmax = fmax(S.rmax, s);
+      const bool conv = s <= a.tol2 * S.bb;
+      S.action = (conv || s < a.delta2 * S.rmax || S.it >= a.maxit) ? 1 : 0;
+    });
+    if (S.action == 1) {
       // reliable update: x_hi += x, r = b - A x_hi in FP64
 #pragma unroll
       for (int k = 0; k < SPT; ++k) {
@@ -238,34 +280,45 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_cg_chain_mixed(ChainCgArgs
         }
       }
       __syncthreads();
-      rr_true = true_residual(a, ci, lshift, red, [&](int k, int, const Sp<double>& rv) {
-#pragma unroll
-        for (int j = 0; j < SPT; ++j)
-          if (j == k) r[j] = to_flt(rv);
+      const double* r64 = a.r64;
+      const double rt = true_residual(a, ci, lshift, red, [&](int, int l, const Sp<double>& rv) {
+        st_sp(const_cast<double*>(r64), ci.off + l, rv);
       });
-      ++updates;
-      if (!isfinite(rr_true)) {
-        flags |= 2;
-        break;
+#pragma unroll
+      for (int k = 0; k < SPT; ++k) {
+        const int l = threadIdx.x + k * blockDim.x;
+        if (l < V) r[k] = to_flt(ld_sp_cg(a.r64, ci.off + l));
       }
-      if (rr_true <= a.tol2 * bb) break;
-      if (it >= a.maxit) {
-        flags |= 1;
-        break;
+      if (threadIdx.x == 0) {
+        S.rr_true = rt;
+        S.updates += 1;
+        if (!isfinite(rt)) {
+          S.flags |= 2;
+          S.action = 2;
+        } else if (rt <= a.tol2 * S.bb) {
+          S.action = 2;
+        } else if (S.it >= a.maxit) {
+          S.flags |= 1;
+          S.action = 2;
+        } else {
+          S.beta = (float)(rt / S.rr_prev);
+          S.rr = rt;
+          S.rmax = rt;
+          S.action = 0;
+        }
       }
-      beta = rr_true / rr_prev;
-      rr = rr_true;
-      rmax = rr_true;
+      __syncthreads();
     }
   }
   if (threadIdx.x == 0) {
-    cc->bb = bb;
-    cc->rr = rr;
-    cc->rr_true = rr_true;
-    cc->iters = it;
-    cc->flags = flags;
+    CgChain* cc = a.cgc + c;
+    cc->bb = S.bb;
+    cc->rr = S.rr;
+    cc->rr_true = S.rr_true;
+    cc->iters = S.it;
+    cc->flags = S.flags;
     cc->state = 0;
-    cc->need_update = updates;  // reports the number of reliable updates
+    cc->need_update = S.updates;  // reports the number of reliable updates
   }
 }
 
@@ -376,26 +429,29 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
   a.delta2 = cg.delta * cg.delta;
   a.maxit = cg.maxit;
   const dim3 grid((unsigned)L->nchains), block(kChainThreads);
+  (void)block;
   if (cg.prec == SM_MIXED) {
     int vmax = 0;
     for (const ChainInfo& ci : L->chains) vmax = ci.L * ci.T > vmax ? ci.L * ci.T : vmax;
     const size_t smem = (size_t)3 * vmax * sizeof(float4);
-    const int spt = (vmax + kChainThreads - 1) / kChainThreads;
+    // x and r of every site live in registers: 8 floats per site, so the
+    // largest chains use 512 threads with 8 sites each (up to 128 registers
+    // per thread) rather than 1024 threads with 4 (64 registers: spills).
     cudaError_t e = cudaSuccess;
-    if (spt <= 1) {
-      e = cudaFuncSetAttribute(k_cg_chain_mixed<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_cg_chain_mixed<1><<<grid, block, smem, c.s>>>(a);
-    } else if (spt <= 2) {
-      e = cudaFuncSetAttribute(k_cg_chain_mixed<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_cg_chain_mixed<2><<<grid, block, smem, c.s>>>(a);
-    } else {
-      e = cudaFuncSetAttribute(k_cg_chain_mixed<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_cg_chain_mixed<4><<<grid, block, smem, c.s>>>(a);
-    }
+    auto go = [&](auto kern, int nt) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) kern<<<grid, dim3(nt), smem, c.s>>>(a);
+    };
+    if (vmax <= 1024)
+      go(k_cg_chain_mixed<1, 1024>, 1024);
+    else if (vmax <= 2048)
+      go(k_cg_chain_mixed<2, 1024>, 1024);
+    else
+      go(k_cg_chain_mixed<8, 512>, 512);
     if (e != cudaSuccess) return fail(SM_ERR_CUDA, "chain CG attribute: %s", cudaGetErrorString(e));
     return launched(c.st, "cg_chain_mixed");
   }
-  k_cg_chain_f64<<<grid, block, 0, c.s>>>(a);
+  k_cg_chain_f64<<<grid, dim3(kChainThreads), 0, c.s>>>(a);
   return launched(c.st, "cg_chain_f64");
 }
 

@@ -423,6 +423,8 @@ int sm_hmc_trajectory(const sm_lattice* lat, double* q, const double* p0, const 
   const int nc = lat->nchains;
   const size_t lbytes = sizeof(double) * 2 * (size_t)lat->N;
   const sm_cg_params& cg = md->cg;
+  sm_cg_params cgH = cg;  // the S_F solves of H
+  if (md->tol_action > 0.0) cgH.tol = md->tol_action;
   double* out = c.w.out;  // [8][nc]: K0, SG0, SF0, K1, SG1, SF1
   c.strict = false;       // a failing chain is rejected, the others go on
 
@@ -431,7 +433,7 @@ int sm_hmc_trajectory(const sm_lattice* lat, double* q, const double* p0, const 
   SM_TRY(launch_dslash<double>(c, c.w.U64, eta, c.w.phi, true, nullptr, 0.0));
   SM_CU(cudaMemcpyAsync(c.w.qsave, q, lbytes, cudaMemcpyDeviceToDevice, c.s));
   SM_CU(cudaMemcpyAsync(c.w.pw, p0, lbytes, cudaMemcpyDeviceToDevice, c.s));
-  SM_TRY(cg_solve(c, c.w.U64, c.w.U32, c.w.phi, c.w.xi, cg, nullptr, nullptr));
+  SM_TRY(cg_solve(c, c.w.U64, c.w.U32, c.w.phi, c.w.xi, cgH, nullptr, nullptr));
   SM_TRY(launch_energies(c, q, c.w.pw, c.w.phi, c.w.xi, out, out + nc, out + 2 * nc));
 
   // molecular dynamics
@@ -439,7 +441,7 @@ int sm_hmc_trajectory(const sm_lattice* lat, double* q, const double* p0, const 
 
   // H at the end
   SM_TRY(make_links(c, q, c.w.U64, c.w.U32, cg));
-  SM_TRY(cg_solve(c, c.w.U64, c.w.U32, c.w.phi, c.w.xi, cg, nullptr, nullptr));
+  SM_TRY(cg_solve(c, c.w.U64, c.w.U32, c.w.phi, c.w.xi, cgH, nullptr, nullptr));
   SM_TRY(launch_energies(c, q, c.w.pw, c.w.phi, c.w.xi, out + 3 * nc, out + 4 * nc, out + 5 * nc));
   std::vector<double> h(6 * (size_t)nc);
   SM_CU(cudaMemcpyAsync(h.data(), out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c.s));

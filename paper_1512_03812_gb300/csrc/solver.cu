@@ -441,14 +441,6 @@ int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, doubl
   std::vector<CgChain> h(c.L->nchains);
   SM_CU(cudaMemcpyAsync(h.data(), c.w.cgc, sizeof(CgChain) * h.size(), cudaMemcpyDeviceToHost, c.s));
   SM_CU(cudaStreamSynchronize(c.s));
-  c.st->cg_solves++;
-  c.st->cg_iterations += batched;
-  if (g_prof.on) {
-    g_prof.batched += batched;
-    for (int i = 0; i < c.L->nchains; ++i)
-      g_prof.site_iters += (long long)h[i].iters * c.L->chains[i].L * c.L->chains[i].T;
-  }
-  c.st->reliable_updates += updates;
   if (chain) {
     int mx = 0;
     for (const CgChain& ch : h) {
@@ -456,8 +448,14 @@ int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, doubl
       updates += ch.need_update;
     }
     batched = mx;
-    c.st->reliable_updates += updates;
-    updates = 0;
+  }
+  c.st->cg_solves++;
+  c.st->cg_iterations += batched;
+  c.st->reliable_updates += updates;
+  if (g_prof.on) {
+    g_prof.batched += batched;
+    for (int i = 0; i < c.L->nchains; ++i)
+      g_prof.site_iters += (long long)h[i].iters * c.L->chains[i].L * c.L->chains[i].T;
   }
   int worst = SM_OK;
   if (!c.strict && c.chain_flags.size() != h.size()) c.chain_flags.assign(h.size(), 0);
