@@ -198,6 +198,29 @@ int sm_apply_D(const sm_lattice* lat, const void* U, const void* in, void* out, 
 int sm_apply_DdagD(const sm_lattice* lat, const void* U, const void* in, void* out, int prec,
                    void* ws, size_t ws_bytes, void* stream);
 
+/* out = D^dag D in for ONE L x T lattice (sides >= 2, periodic x,
+ * antiperiodic t, bare mass m0), without allocating anything.  The paper has
+ * no counterpart: this is a service for callers that cannot call cudaMalloc
+ * -- code whose device memory is all owned by a host framework's pool, code
+ * that must not risk the device-wide synchronisation of an allocation, or
+ * plugins that may not create allocations -- and therefore can create neither
+ * a workspace nor a lattice object (sm_lattice_create allocates).
+ * U, in, out as for sm_apply_D (prec SM_F64 or SM_F32, sites n = x + L t,
+ * U with the antiperiodic sign folded in as written by sm_links); in and out
+ * must not overlap.  The intermediate D in is kept in a built-in device array
+ * of 8 MiB: at most 262144 sites in FP64 or 524288 in FP32; larger lattices
+ * are rejected with SM_ERR_ARG.  The array is loaded with the library on
+ * every GPU that uses it and held until the process exits.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All
+ * calls share the one array and each overwrites it completely before reading
+ * it, so nothing carries over between calls -- but calls whose work can
+ * overlap on the GPU (different streams, or concurrent host threads) race on
+ * it and must be serialised by the caller.  Enqueues on `stream`, returns
+ * without synchronising. */
+int sm_apply_DdagD_noalloc(int L, int T, double m0, const void* U, const void* in, void* out,
+                           int prec, void* stream);
+
 /* -------------------------------------------------------- inversion ------- */
 
 /* Solves D^dag D x = b for every chain (Sec. 3: the inversions behind

@@ -88,6 +88,8 @@ _SIGS = {
     "sm_links": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "sm_apply_D": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P]),
     "sm_apply_DdagD": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _P, ctypes.c_size_t, _P]),
+    "sm_apply_DdagD_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _P,
+                                              _P, _P, ctypes.c_int, _P]),
     "sm_cg_solve": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(CgParams), _P,
                                    ctypes.c_size_t, _P, _P, _P]),
     "sm_gauge_force": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -338,6 +340,18 @@ class Lattice:
         if check or rc not in (SM_ERR_NAN, SM_ERR_NOT_CONVERGED):
             _check(rc)
         return dH, H0, acc.astype(bool)
+
+
+def apply_DdagD_noalloc(L: int, T: int, m0: float, U, psi, out=None):
+    """D^dag D psi for one L x T lattice through the entry point that
+    allocates nothing (sm_apply_DdagD_noalloc); for callers that cannot
+    create a workspace or a lattice object."""
+    lib = load()
+    prec = SM_F64 if psi.dtype == torch.complex128 else SM_F32
+    out = torch.empty_like(psi) if out is None else out
+    _check(lib.sm_apply_DdagD_noalloc(int(L), int(T), float(m0), _ptr(U), _ptr(psi), _ptr(out),
+                                      prec, _stream()))
+    return out
 
 
 def profile_enable(on: bool = True) -> None:
