@@ -237,6 +237,18 @@ def run_ours(args):
         flush.fill_(1)  # evict the previous step's working set from L2
         return lat.hmc_trajectory(q, p, e, u, md, check=False)
 
+    # pick the chain-resident CG kernel for this batch (untimed): time every
+    # applicable variant on one representative solve at the start links
+    tune = None
+    if args.prec == "mixed" and args.algo != "grid":
+        U64s, U32s = lat.links(q_start)
+        b_t = torch.view_as_complex(torch.randn((N, 2, 2), generator=gen, device=dev,
+                                                dtype=torch.float64)).contiguous()
+        v, vms = lat.autotune_cg(U64s, U32s, b_t, cgp)
+        tune = {"variant": v, "ms_per_variant": [round(t, 3) for t in vms]}
+        log(f"autotuned chain CG: variant {v}, ms {vms}")
+        del U64s, U32s, b_t
+
     q = q_start.clone()
     pw, ew, uw = draws(args.warmup)
     for i in range(args.warmup):
@@ -361,6 +373,10 @@ def run_ours(args):
     roofline.update({"site_iters": prof["site_iters"], "kernel_ms": round(prof["iter_ms"], 3),
                      "kernel_share_of_step": round(prof["iter_ms"] / ms, 4)})
 
+    ddagd = None
+    if not args.no_ddagd:
+        ddagd = {"f32": measure_ddagd(torch, P, dev, prec="f32"),
+                 "f64": measure_ddagd(torch, P, dev, prec="f64")}
     if rank != 0:
         return
     cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu) else None
@@ -371,17 +387,58 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32+f64" if args.prec == "mixed" else "f64",
         "data": "synthetic (own thermalised start, seeded momenta/noise)",
         "config": dict(W, chains_per_gpu=B, precision=args.prec, parallelism=f"replicas{world}",
-                       l2="flushed between steps (256 MiB write)"),
+                       l2="flushed between steps (256 MiB write)", cg_autotune=tune),
         "acceptance": round(acc_rate, 4),
         "e2e": {"value": round(aggregate(world, B, K, e2e_ms), 3), "unit": "trajectories/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roofline,
         "fp64": fp64,
+        "ddagd_2048": ddagd,
         "clocks": clk,
         "cpu_baseline": cpu,
     }
     print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------- D^dag D at 2048 x 2048 --
+
+def measure_ddagd(torch, P, dev, reps=20, prec="f32"):
+    """Fused D^dag D (sm_apply_DdagD) on one 2048 x 2048 lattice: CUDA-event
+    time per launch with L2 flushed before each launch; algorithmic bytes
+    48 (FP32) or 96 (FP64) per site: read in and U once, write out once."""
+    L = T = 2048
+    lat = P.Lattice(L, T, 8.0, kappa_to_m0(0.255), device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    q = (torch.rand((L * T, 2), generator=g, device=dev, dtype=torch.float64) * 2 - 1) * math.pi
+    U64, U32 = lat.links(q)
+    cdt = torch.complex64 if prec == "f32" else torch.complex128
+    psi = torch.randn((L * T, 2), generator=g, device=dev, dtype=cdt)
+    out = torch.empty_like(psi)
+    U = U32 if prec == "f32" else U64
+    flush = torch.empty(int(256 * 2 ** 20), dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        lat.apply_DdagD(U, psi, out)
+    ts = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(reps):
+        flush.fill_(2)
+        e0.record()
+        lat.apply_DdagD(U, psi, out)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.median(ts))
+    bps = 48 if prec == "f32" else 96
+    gbs = bps * L * T / (ms / 1e3) / 1e9
+    peaks, src = measured_peaks()
+    return {"kernel": f"k_ddagd_tile<{'float' if prec == 'f32' else 'double'}>", "lattice": "2048x2048",
+            "ms_median": round(ms, 4), "bytes_per_site": bps, "achieved": round(gbs, 1),
+            "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+            "frac": round(gbs / float(peaks["hbm_gbs"]), 4), "peak_source": src,
+            "l2": "flushed before each launch", "reps": reps}
 
 
 # ------------------------------------------------------- oracle (CPU) ------
@@ -440,6 +497,7 @@ def main():
     ap.add_argument("--therm", type=int, default=20)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ddagd", action="store_true")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])
     ap.add_argument("--M", type=int, default=WORKLOAD["M"])
     ap.add_argument("--delta", type=float, default=0.01)

@@ -194,7 +194,8 @@ int sm_links(const sm_lattice* lat, const double* q, double* U64, float* U32, vo
 int sm_apply_D(const sm_lattice* lat, const void* U, const void* in, void* out, int dagger,
                int prec, void* stream);
 
-/* out = D^dag D in (Eq. fer_action), same conventions as sm_apply_D. */
+/* out = D^dag D in (Eq. fer_action), same conventions as sm_apply_D, in one
+ * fused pass (D in is kept on chip per tile).  ws is not used (may be NULL). */
 int sm_apply_DdagD(const sm_lattice* lat, const void* U, const void* in, void* out, int prec,
                    void* ws, size_t ws_bytes, void* stream);
 
@@ -233,6 +234,20 @@ int sm_apply_DdagD_noalloc(int L, int T, double m0, const void* U, const void* i
 int sm_cg_solve(const sm_lattice* lat, const double* U64, const float* U32, const double* b,
                 double* x, const sm_cg_params* cg, void* ws, size_t ws_bytes, int* iters,
                 double* relres, void* stream);
+
+/* Autotuner of the chain-resident mixed-precision CG: times every kernel
+ * variant that applies to this lattice's chain shapes (0: strided layout,
+ * any chain up to 4096 sites; 1: column layout, 512 threads x 8 rows; 2:
+ * column layout, 256 threads x 16 rows) on the given solve (b, FP64; x is
+ * overwritten), and stores the fastest in the lattice object, which later
+ * SM_MIXED chain-resident solves use.  variant (host, may be NULL) receives
+ * the choice, ms (host [3], may be NULL) each variant's time or -1 where it
+ * does not apply.  The variants differ only in their reduction order: results
+ * agree to rounding, and a lattice object gives reproducible results once
+ * tuned.  Needs SM_MIXED and chains of at most 4096 sites.  Synchronises. */
+int sm_autotune_cg(sm_lattice* lat, const double* U64, const float* U32, const double* b,
+                   double* x, const sm_cg_params* cg, void* ws, size_t ws_bytes, int* variant,
+                   double* ms, void* stream);
 
 /* ----------------------------------------------------------- forces ------- */
 

@@ -92,6 +92,8 @@ _SIGS = {
                                               _P, _P, ctypes.c_int, _P]),
     "sm_cg_solve": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(CgParams), _P,
                                    ctypes.c_size_t, _P, _P, _P]),
+    "sm_autotune_cg": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(CgParams), _P,
+                                      ctypes.c_size_t, _P, _P, _P]),
     "sm_gauge_force": (ctypes.c_int, [_P, _P, _P, _P]),
     "sm_fermion_force": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(CgParams), _P, _P,
                                         ctypes.c_size_t, ctypes.POINTER(Stats), _P]),
@@ -261,6 +263,19 @@ class Lattice:
                                 ctypes.byref(p), *self._ws(), iters.ctypes.data,
                                 relres.ctypes.data, _stream()))
         return x, iters, relres
+
+    def autotune_cg(self, U64, U32, b, cg: CG):
+        """Times the chain-resident CG kernel variants on this solve and
+        keeps the fastest for this lattice (sm_autotune_cg); returns
+        (variant, [ms per variant or -1])."""
+        x = torch.empty_like(b)
+        v = ctypes.c_int()
+        ms = np.zeros(3)
+        p = cg.c()
+        _check(_LIB.sm_autotune_cg(self._h, _ptr(U64), _ptr(U32), _ptr(b), _ptr(x),
+                                   ctypes.byref(p), *self._ws(), ctypes.byref(v), ms.ctypes.data,
+                                   _stream()))
+        return v.value, ms.tolist()
 
     def gauge_force(self, q, F=None):
         F = self.field() if F is None else F

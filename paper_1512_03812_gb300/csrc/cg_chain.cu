@@ -322,6 +322,180 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_mixed(ChainCgArgs a) {
   }
 }
 
+// Column layout for chains whose shape matches the block: thread tid owns
+// column x = tid % L and the R consecutive rows t0 .. t0 + R - 1 of row block
+// tid / L.  D and D^dag walk down the column with a sliding window, so the
+// t-neighbours and U_t(n - t) come from registers and only the x-neighbours
+// and the links of the site are read from shared memory.  Every warp
+// finishes the block sums itself (FP32, the same order in every warp), so
+// all threads hold identical scalars and an iteration needs three barriers.
+template <int R, int NT>
+__global__ void __launch_bounds__(NT, 1) k_cg_chain_col(ChainCgArgs a) {
+  extern __shared__ float4 smem[];
+  __shared__ float red[2][NT / 32];
+  __shared__ double redd[33];
+  const int c = a.list[blockIdx.x];
+  const ChainInfo ci = a.chains[c];
+  const int L = ci.L, T = ci.T, V = L * T;
+  float4* Us = smem;
+  float4* ps = smem + V;
+  float4* ts = smem + 2 * V;
+  const float diag = (float)(2.0 + ci.m0);
+  const int x = threadIdx.x % L, t0 = (threadIdx.x / L) * R;
+  const int xp = x + 1 == L ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  auto site = [&](int t) { return (t < 0 ? t + T : (t >= T ? t - T : t)) * L; };
+
+  // sum of one FP32 value per thread, finished by every warp
+  auto bsum = [&](float v, float* buf) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) buf[w] = v;
+    __syncthreads();
+    float s = lane < NT / 32 ? buf[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+  };
+
+  Sp<float> xv[R], rv[R];
+  double bbl = 0.0;
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int l = x + (t0 + j) * L;
+    Us[l] = __ldg(reinterpret_cast<const float4*>(a.U32) + ci.off + l);
+    const Sp<double> bv = ld_sp(a.b, ci.off + l);
+    bbl += norm2(bv);
+    rv[j] = to_flt(bv);
+    xv[j] = {{0.f, 0.f}, {0.f, 0.f}};
+    ps[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+    st_sp(a.x, ci.off + l, Sp<double>{{0, 0}, {0, 0}});
+  }
+  const double bb = cta_sum(bbl, redd);
+  // scalars, identical in every thread
+  float rr = (float)bb, rr_prev = rr, rmax = rr, beta = 0.f;
+  const float tol2bb = (float)(a.tol2 * bb), delta2 = (float)a.delta2;
+  double rr_true = bb;
+  int it = 0, flags = isfinite(bb) ? 0 : 2, updates = 0;
+  bool run = bb > 0.0 && isfinite(bb);
+
+  while (run) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int l = x + (t0 + j) * L;
+      ps[l] = f4_of(rv[j] + beta * sp_of(ps[l]));
+    }
+    __syncthreads();
+    // t = D p down the column
+    float pap = 0.f;
+    {
+      int rb = site(t0 - 1);
+      Sp<float> pm = sp_of(ps[x + rb]), pc = sp_of(ps[x + t0 * L]);
+      float4 um = Us[x + rb];
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int row = (t0 + j) * L, rn = site(t0 + j + 1);
+        const Sp<float> pn = sp_of(ps[x + rn]);
+        const float4 u = Us[x + row];
+        const float4 uxm = Us[xm + row];
+        const Sp<float> o = hop_sum<false, float>(sp_of(ps[xp + row]), sp_of(ps[xm + row]), pn,
+                                                  pm, {u.x, u.y}, {uxm.x, uxm.y}, {u.z, u.w},
+                                                  {um.z, um.w});
+        const Sp<float> tv = diag * pc - 0.5f * o;
+        ts[x + row] = f4_of(tv);
+        pap += norm2(tv);
+        pm = pc;
+        pc = pn;
+        um = u;
+        asm volatile("" ::: "memory");  // keep the next row's loads after this row
+      }
+    }
+    const float papt = bsum(pap, red[0]);  // its barrier also publishes ts
+    if (!(papt > 0.f) || !isfinite(papt)) {
+      flags |= 2;
+      break;
+    }
+    const float alpha = rr / papt;
+    // A p = D^dag t down the column; x += alpha p; r -= alpha A p
+    float rn2 = 0.f;
+    {
+      int rb = site(t0 - 1);
+      Sp<float> tm = sp_of(ts[x + rb]), tc = sp_of(ts[x + t0 * L]);
+      float4 um = Us[x + rb];
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int row = (t0 + j) * L, rn = site(t0 + j + 1);
+        const Sp<float> tn = sp_of(ts[x + rn]);
+        const float4 u = Us[x + row];
+        const float4 uxm = Us[xm + row];
+        const Sp<float> o = hop_sum<true, float>(sp_of(ts[xp + row]), sp_of(ts[xm + row]), tn, tm,
+                                                 {u.x, u.y}, {uxm.x, uxm.y}, {u.z, u.w},
+                                                 {um.z, um.w});
+        const Sp<float> Ap = diag * tc - 0.5f * o;
+        xv[j] = xv[j] + alpha * sp_of(ps[x + row]);
+        rv[j] = rv[j] - alpha * Ap;
+        rn2 += norm2(rv[j]);
+        tm = tc;
+        tc = tn;
+        um = u;
+        asm volatile("" ::: "memory");
+      }
+    }
+    const float rrn = bsum(rn2, red[1]);
+    rr_prev = rr;
+    rr = rrn;
+    beta = rr / rr_prev;
+    ++it;
+    if (!isfinite(rr)) {
+      flags |= 2;
+      break;
+    }
+    rmax = fmaxf(rmax, rr);
+    if (rr <= tol2bb || rr < delta2 * rmax || it >= a.maxit) {
+      // reliable update: x_hi += x, r = b - A x_hi in FP64
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const long long n = ci.off + x + (t0 + j) * L;
+        st_sp(a.x, n, ld_sp_cg(a.x, n) + to_dbl(xv[j]));
+        xv[j] = {{0.f, 0.f}, {0.f, 0.f}};
+      }
+      __syncthreads();
+      const double* r64 = a.r64;
+      const int lshift = (L & (L - 1)) == 0 ? __ffs(L) - 1 : -1;
+      rr_true = true_residual(a, ci, lshift, redd, [&](int, int l, const Sp<double>& r) {
+        st_sp(const_cast<double*>(r64), ci.off + l, r);
+      });
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < R; ++j) rv[j] = to_flt(ld_sp_cg(a.r64, ci.off + x + (t0 + j) * L));
+      ++updates;
+      if (!isfinite(rr_true)) {
+        flags |= 2;
+        break;
+      }
+      if (rr_true <= a.tol2 * bb) break;
+      if (it >= a.maxit) {
+        flags |= 1;
+        break;
+      }
+      beta = (float)(rr_true / (double)rr_prev);
+      rr = (float)rr_true;
+      rmax = rr;
+    }
+    __syncthreads();  // ts and ps reads of this iteration are done
+  }
+  if (threadIdx.x == 0) {
+    CgChain* cc = a.cgc + c;
+    cc->bb = bb;
+    cc->rr = rr;
+    cc->rr_true = rr_true;
+    cc->iters = it;
+    cc->flags = flags;
+    cc->state = 0;
+    cc->need_update = updates;
+  }
+}
+
 // FP64: the same iteration with all fields in global memory (x is the output,
 // r64, p64, t64 scratch), one block per chain.
 __global__ void __launch_bounds__(kChainThreads, 1) k_cg_chain_f64(ChainCgArgs a) {
@@ -401,6 +575,19 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_cg_chain_f64(ChainCgArgs a
   }
 }
 
+// Kernel variants of the mixed chain-resident solve: 0 the strided layout
+// (any chain up to 4096 sites), 1 the column layout with 512 threads x 8
+// rows, 2 the column layout with 256 threads x 16 rows (1 and 2 need every
+// chain's shape to match).
+bool chain_variant_applies(const sm_lattice* L, int v) {
+  if (v == 0) return true;
+  const int nt = v == 1 ? 512 : 256, rows = v == 1 ? 8 : 16;
+  if (v != 1 && v != 2) return false;
+  for (const ChainInfo& ci : L->chains)
+    if (nt % ci.L != 0 || ci.T != rows * (nt / ci.L)) return false;
+  return true;
+}
+
 // Largest chain volume the shared-memory FP32 form holds (48 B per site).
 constexpr int kChainMaxVolume = 4096;
 
@@ -434,20 +621,27 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
     int vmax = 0;
     for (const ChainInfo& ci : L->chains) vmax = ci.L * ci.T > vmax ? ci.L * ci.T : vmax;
     const size_t smem = (size_t)3 * vmax * sizeof(float4);
-    // x and r of every site live in registers: 8 floats per site, so the
-    // largest chains use 512 threads with 8 sites each (up to 128 registers
-    // per thread) rather than 1024 threads with 4 (64 registers: spills).
     cudaError_t e = cudaSuccess;
     auto go = [&](auto kern, int nt) {
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e == cudaSuccess) kern<<<grid, dim3(nt), smem, c.s>>>(a);
     };
-    if (vmax <= 1024)
+    int v = L->cg_variant;
+    if (v < 0 || !chain_variant_applies(L, v)) v = 0;
+    if (v == 1) {
+      go(k_cg_chain_col<8, 512>, 512);
+    } else if (v == 2) {
+      go(k_cg_chain_col<16, 256>, 256);
+    } else if (vmax <= 1024) {
+      // x and r of every site live in registers: 8 floats per site, so the
+      // largest chains use 512 threads with 8 sites each (up to 128
+      // registers per thread) rather than 1024 threads with 4 (64: spills).
       go(k_cg_chain_mixed<1, 1024>, 1024);
-    else if (vmax <= 2048)
+    } else if (vmax <= 2048) {
       go(k_cg_chain_mixed<2, 1024>, 1024);
-    else
+    } else {
       go(k_cg_chain_mixed<8, 512>, 512);
+    }
     if (e != cudaSuccess) return fail(SM_ERR_CUDA, "chain CG attribute: %s", cudaGetErrorString(e));
     return launched(c.st, "cg_chain_mixed");
   }

@@ -538,6 +538,7 @@ int sm_lattice_create(int nchains, const int* L, const int* T, const double* bet
   }
   lat->N = off;
   lat->nblocks = blk;
+  lat->cg_variant = -1;
   cudaGetDevice(&lat->device);
   cudaError_t e = cudaMalloc(&lat->d_chains, sizeof(ChainInfo) * nchains);
   if (e == cudaSuccess) e = cudaMalloc(&lat->d_blk_chain, sizeof(int) * blk);
@@ -559,6 +560,11 @@ int sm_lattice_create(int nchains, const int* L, const int* T, const double* bet
     sm_lattice_destroy(lat);
     return fail(SM_ERR_CUDA, "lattice tables: %s", cudaGetErrorString(e));
   }
+  const int rc = build_tile_table(lat);
+  if (rc) {
+    sm_lattice_destroy(lat);
+    return rc;
+  }
   *out = lat;
   return SM_OK;
 }
@@ -568,6 +574,8 @@ int sm_lattice_destroy(sm_lattice* lat) {
   if (lat->d_chains) cudaFree(lat->d_chains);
   if (lat->d_blk_chain) cudaFree(lat->d_blk_chain);
   if (lat->d_chain_list) cudaFree(lat->d_chain_list);
+  if (lat->d_tiles) cudaFree(lat->d_tiles);
+  if (lat->d_tiles_big) cudaFree(lat->d_tiles_big);
   if (lat->h_pinned) cudaFreeHost(lat->h_pinned);
   if (lat->ev[0]) cudaEventDestroy(lat->ev[0]);
   if (lat->ev[1]) cudaEventDestroy(lat->ev[1]);
@@ -609,23 +617,17 @@ int sm_apply_D(const sm_lattice* lat, const void* U, const void* in, void* out, 
 
 int sm_apply_DdagD(const sm_lattice* lat, const void* U, const void* in, void* out, int prec,
                    void* ws, size_t ws_bytes, void* stream) {
+  (void)ws;
+  (void)ws_bytes;
   Ctx c;
-  int rc = c.init(lat, ws, ws_bytes, stream, nullptr);
+  int rc = c.init(lat, nullptr, 0, stream, nullptr);
   if (rc) return rc;
   if (!U || !in || !out) return fail(SM_ERR_ARG, "sm_apply_DdagD: NULL field");
   if (!al16(U) || !al16(in) || !al16(out))
     return fail(SM_ERR_ARG, "sm_apply_DdagD: unaligned field");
   if (in == out) return fail(SM_ERR_ARG, "sm_apply_DdagD: in and out alias");
-  if (prec == SM_F64) {
-    rc = launch_dslash<double>(c, (const double*)U, (const double*)in, c.w.t, false, nullptr, 0.0);
-    if (rc) return rc;
-    return launch_dslash<double>(c, (const double*)U, c.w.t, (double*)out, true, nullptr, 0.0);
-  }
-  if (prec == SM_F32) {
-    rc = launch_dslash<float>(c, (const float*)U, (const float*)in, c.w.t32, false, nullptr, 0.0);
-    if (rc) return rc;
-    return launch_dslash<float>(c, (const float*)U, c.w.t32, (float*)out, true, nullptr, 0.0);
-  }
+  if (prec == SM_F64) return launch_ddagd<double>(c, (const double*)U, (const double*)in, (double*)out);
+  if (prec == SM_F32) return launch_ddagd<float>(c, (const float*)U, (const float*)in, (float*)out);
   return fail(SM_ERR_ARG, "sm_apply_DdagD: prec must be SM_F64 or SM_F32");
 }
 

@@ -18,6 +18,11 @@ struct sm_lattice {
   sm::ChainInfo* d_chains;
   int* d_blk_chain;
   int* d_chain_list;  // [nchains] 0, 1, ..., nchains - 1
+  int4* d_tiles;      // tiles of the fused D^dag D kernel (ddagd.cu)
+  int ntiles;
+  int4* d_tiles_big;  // 64 x 16 tiles of its large-lattice FP32 form
+  int ntiles_big;
+  int cg_variant;     // chain-resident mixed CG kernel chosen by sm_autotune_cg (-1: default)
   int device;
   int* h_pinned;  // small pinned host buffer for per-call readbacks
   cudaEvent_t ev[2];  // readback events of the CG loop
@@ -114,8 +119,15 @@ int launch_energies(Ctx& c, const double* q, const double* p, const double* phi,
                     double* K, double* SG, double* SF);
 int launch_copy_links_masked(Ctx& c, double* dst, const double* src, const int* mask);
 
+// Fused D^dag D (ddagd.cu).
+int build_tile_table(sm_lattice* lat);
+template <typename R>
+int launch_ddagd(Ctx& c, const R* U, const R* in, R* out);
+
 // Chain-resident CG (cg_chain.cu): one block per chain.
 bool chain_cg_fits(const sm_lattice* L, int prec);
+bool chain_variant_applies(const sm_lattice* L, int v);
+constexpr int kChainVariants = 3;
 int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
                     const sm_cg_params& cg);
 

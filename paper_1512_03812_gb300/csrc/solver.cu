@@ -477,6 +477,50 @@ int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, doubl
 
 using namespace sm;
 
+extern "C" int sm_autotune_cg(sm_lattice* lat, const double* U64, const float* U32,
+                              const double* b, double* x, const sm_cg_params* cg, void* ws,
+                              size_t ws_bytes, int* variant, double* ms, void* stream) {
+  Ctx c;
+  int rc = c.init(lat, ws, ws_bytes, stream, nullptr);
+  if (rc) return rc;
+  if (!cg || cg->prec != SM_MIXED || !chain_cg_fits(lat, SM_MIXED))
+    return fail(SM_ERR_ARG, "sm_autotune_cg: needs SM_MIXED and chains of at most 4096 sites");
+  sm_cg_params p = *cg;
+  p.algo = SM_CG_CHAIN;
+  cudaEvent_t e0, e1;
+  SM_CU(cudaEventCreate(&e0));
+  SM_CU(cudaEventCreate(&e1));
+  int best = 0;
+  double best_ms = 1e300;
+  for (int v = 0; v < kChainVariants; ++v) {
+    if (ms) ms[v] = -1.0;
+    if (!chain_variant_applies(lat, v)) continue;
+    lat->cg_variant = v;
+    double t = 1e300;
+    for (int rep = 0; rep < 3; ++rep) {  // the first repetition warms up
+      SM_CU(cudaEventRecord(e0, c.s));
+      rc = cg_solve(c, U64, U32, b, x, p, nullptr, nullptr);
+      if (rc && rc != SM_ERR_NOT_CONVERGED) break;
+      SM_CU(cudaEventRecord(e1, c.s));
+      SM_CU(cudaEventSynchronize(e1));
+      float f = 0.f;
+      SM_CU(cudaEventElapsedTime(&f, e0, e1));
+      if (rep > 0 && f < t) t = f;
+    }
+    if (rc && rc != SM_ERR_NOT_CONVERGED) break;
+    if (ms) ms[v] = t;
+    if (t < best_ms) {
+      best_ms = t;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  lat->cg_variant = best;
+  if (variant) *variant = best;
+  return rc == SM_ERR_NOT_CONVERGED ? SM_OK : rc;
+}
+
 extern "C" int sm_profile_enable(int on) {
   if (on && !g_prof.ready) {
     for (int i = 0; i < 2; ++i) {

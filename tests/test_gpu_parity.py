@@ -79,6 +79,21 @@ def test_apply_DdagD(torch):
         assert rel_err(b.chain(out32, c), ref) < 4e-6
 
 
+def test_apply_DdagD_large_batch_tiles(torch):
+    """Batches of 2^18 sites or more take the 64 x 16-tile FP32 form; with a
+    512 x 512 chain in the batch the small and odd lattices beside it (tiles
+    larger than the lattice, periodic wrap) go through it too."""
+    dims = [(512, 512)] + DIMS
+    b = batch(torch, dims=dims)
+    assert b.lat.N >= 2 ** 18
+    q, psi = b.q(), b.spinor()
+    U64, U32 = b.lat.links(b.dev(q))
+    out32 = b.lat.apply_DdagD(U32, b.dev(psi, torch.complex64))
+    for c, ol in enumerate(b.olat):
+        ref = sw.apply_DdagD(ol, sw.links(b.chain(q, c)), b.chain(psi, c))
+        assert rel_err(b.chain(out32, c), ref) < 4e-6, dims[c]
+
+
 @pytest.mark.parametrize("algo", ["grid", "chain"])
 def test_cg_f64_matches_oracle(torch, algo):
     b = batch(torch)
