@@ -245,7 +245,9 @@ def run_ours(args):
         b_t = torch.view_as_complex(torch.randn((N, 2, 2), generator=gen, device=dev,
                                                 dtype=torch.float64)).contiguous()
         v, vms = lat.autotune_cg(U64s, U32s, b_t, cgp)
-        tune = {"variant": v, "ms_per_variant": [round(t, 3) for t in vms]}
+        tune = {"variant": v, "ms_per_variant": [round(t, 3) for t in vms],
+                "variants": ["strided 512x8", "column 512x8", "column 256x16",
+                             "column 2-block cluster 256x8"]}
         log(f"autotuned chain CG: variant {v}, ms {vms}")
         del U64s, U32s, b_t
 

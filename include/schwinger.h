@@ -238,16 +238,22 @@ int sm_cg_solve(const sm_lattice* lat, const double* U64, const float* U32, cons
 /* Autotuner of the chain-resident mixed-precision CG: times every kernel
  * variant that applies to this lattice's chain shapes (0: strided layout,
  * any chain up to 4096 sites; 1: column layout, 512 threads x 8 rows; 2:
- * column layout, 256 threads x 16 rows) on the given solve (b, FP64; x is
- * overwritten), and stores the fastest in the lattice object, which later
- * SM_MIXED chain-resident solves use.  variant (host, may be NULL) receives
- * the choice, ms (host [3], may be NULL) each variant's time or -1 where it
- * does not apply.  The variants differ only in their reduction order: results
+ * column layout, 256 threads x 16 rows; 3: column layout split over a
+ * cluster of two blocks, 256 threads x 8 rows each, rows exchanged through
+ * distributed shared memory) on the given solve (b, FP64; x is overwritten),
+ * and stores the fastest in the lattice object, which later SM_MIXED
+ * chain-resident solves use.  variant (host, may be NULL) receives the
+ * choice, ms (host [4], may be NULL) each variant's time or -1 where it does
+ * not apply.  The variants differ only in their reduction order: results
  * agree to rounding, and a lattice object gives reproducible results once
  * tuned.  Needs SM_MIXED and chains of at most 4096 sites.  Synchronises. */
 int sm_autotune_cg(sm_lattice* lat, const double* U64, const float* U32, const double* b,
                    double* x, const sm_cg_params* cg, void* ws, size_t ws_bytes, int* variant,
                    double* ms, void* stream);
+
+/* Pins the kernel variant of the chain-resident mixed CG (as numbered for
+ * sm_autotune_cg; -1 restores the default).  SM_ERR_ARG if it does not fit. */
+int sm_set_cg_variant(sm_lattice* lat, int variant);
 
 /* ----------------------------------------------------------- forces ------- */
 

@@ -94,6 +94,7 @@ _SIGS = {
                                    ctypes.c_size_t, _P, _P, _P]),
     "sm_autotune_cg": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(CgParams), _P,
                                       ctypes.c_size_t, _P, _P, _P]),
+    "sm_set_cg_variant": (ctypes.c_int, [_P, ctypes.c_int]),
     "sm_gauge_force": (ctypes.c_int, [_P, _P, _P, _P]),
     "sm_fermion_force": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(CgParams), _P, _P,
                                         ctypes.c_size_t, ctypes.POINTER(Stats), _P]),
@@ -270,12 +271,16 @@ class Lattice:
         (variant, [ms per variant or -1])."""
         x = torch.empty_like(b)
         v = ctypes.c_int()
-        ms = np.zeros(3)
+        ms = np.zeros(4)
         p = cg.c()
         _check(_LIB.sm_autotune_cg(self._h, _ptr(U64), _ptr(U32), _ptr(b), _ptr(x),
                                    ctypes.byref(p), *self._ws(), ctypes.byref(v), ms.ctypes.data,
                                    _stream()))
         return v.value, ms.tolist()
+
+    def set_cg_variant(self, variant: int):
+        """Pins the chain-resident mixed CG kernel variant (-1: default)."""
+        _check(_LIB.sm_set_cg_variant(self._h, int(variant)))
 
     def gauge_force(self, q, F=None):
         F = self.field() if F is None else F

@@ -11,6 +11,7 @@
 // reliable update (x_hi += x; r = b - D^dag D x_hi) reads and writes the
 // FP64 fields in global memory.  In the FP64 form all fields stay in global
 // memory (L2-resident for small chains) and the block still iterates alone.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -496,6 +497,212 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_col(ChainCgArgs a) {
   }
 }
 
+// The column layout split over a cluster of two blocks: block rank k owns the
+// rows [k T/2, (k+1) T/2) of the chain (U, p, t of those rows in its shared
+// memory: 96 KB at 64 x 64, so two blocks fit on one SM and 200 chains fill
+// 152 SMs in about 1.5 waves instead of 2).  The rows just below and above
+// a block's half are read from the other block's shared memory (distributed
+// shared memory), and block sums are combined through it.  Every decision is
+// taken on sums that both blocks add in the same order (rank 0's part plus
+// rank 1's part), so both execute the same sequence of cluster barriers; a
+// final barrier keeps either block from exiting while the other may still
+// read its shared memory.
+template <int R, int NT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT, 2)
+    k_cg_chain_cluster(ChainCgArgs a) {
+  namespace cgr = cooperative_groups;
+  cgr::cluster_group cl = cgr::this_cluster();
+  extern __shared__ float4 smem[];
+  __shared__ float red[2][NT / 32];
+  __shared__ double redd[33];
+  __shared__ float slot[2];   // this block's part of the two sums of an iteration
+  __shared__ double slotd;    // this block's part of an FP64 sum
+  const unsigned rank = cl.block_rank();
+  const int c = a.list[blockIdx.x >> 1];
+  const ChainInfo ci = a.chains[c];
+  const int L = ci.L, T = ci.T, H = T / 2, HV = H * L;
+  const long long base = ci.off + (long long)rank * HV;  // first global site of this half
+  float4* Us = smem;
+  float4* ps = smem + HV;
+  float4* ts = smem + 2 * HV;
+  float4* Up = cl.map_shared_rank(Us, rank ^ 1);
+  float4* pp = cl.map_shared_rank(ps, rank ^ 1);
+  float4* tp = cl.map_shared_rank(ts, rank ^ 1);
+  float* slot0 = cl.map_shared_rank(slot, 0);
+  float* slot1 = cl.map_shared_rank(slot, 1);
+  double* slotd0 = cl.map_shared_rank(&slotd, 0);
+  double* slotd1 = cl.map_shared_rank(&slotd, 1);
+  const float diag = (float)(2.0 + ci.m0);
+  const int x = threadIdx.x % L, t0 = (threadIdx.x / L) * R;  // local rows t0 .. t0 + R - 1
+  const int xp = x + 1 == L ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // local row -1 is the other half's last row, local row H its first row
+  auto at = [&](const float4* own, const float4* peer, int lr, int xx) {
+    return lr < 0 ? peer[(H - 1) * L + xx] : (lr >= H ? peer[xx] : own[lr * L + xx]);
+  };
+  // block sum (FP32, finished by every warp), then the cluster sum
+  auto csum = [&](float v, int k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[k][w] = v;
+    __syncthreads();
+    float s = lane < NT / 32 ? red[k][lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) slot[k] = s;
+    cl.sync();
+    return slot0[k] + slot1[k];
+  };
+  auto csumd = [&](double v) {
+    const double s = cta_sum(v, redd);
+    if (threadIdx.x == 0) slotd = s;
+    cl.sync();
+    const double tot = *slotd0 + *slotd1;
+    cl.sync();  // both have read before slotd is written again
+    return tot;
+  };
+
+  Sp<float> xv[R], rv[R];
+  double bbl = 0.0;
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int l = x + (t0 + j) * L;
+    Us[l] = __ldg(reinterpret_cast<const float4*>(a.U32) + base + l);
+    const Sp<double> bv = ld_sp(a.b, base + l);
+    bbl += norm2(bv);
+    rv[j] = to_flt(bv);
+    xv[j] = {{0.f, 0.f}, {0.f, 0.f}};
+    ps[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+    st_sp(a.x, base + l, Sp<double>{{0, 0}, {0, 0}});
+  }
+  const double bb = csumd(bbl);
+  float rr = (float)bb, rr_prev = rr, rmax = rr, beta = 0.f;
+  const float tol2bb = (float)(a.tol2 * bb), delta2 = (float)a.delta2;
+  double rr_true = bb;
+  int it = 0, flags = isfinite(bb) ? 0 : 2, updates = 0;
+  bool run = bb > 0.0 && isfinite(bb);
+
+  while (run) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int l = x + (t0 + j) * L;
+      ps[l] = f4_of(rv[j] + beta * sp_of(ps[l]));
+    }
+    cl.sync();  // both halves' p (and, first time round, U) are written
+    float pap = 0.f;
+    {
+      Sp<float> pm = sp_of(at(ps, pp, t0 - 1, x)), pc = sp_of(ps[t0 * L + x]);
+      float4 um = at(Us, Up, t0 - 1, x);
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int row = (t0 + j) * L;
+        const Sp<float> pn = sp_of(at(ps, pp, t0 + j + 1, x));
+        const float4 u = Us[x + row];
+        const float4 uxm = Us[xm + row];
+        const Sp<float> o = hop_sum<false, float>(sp_of(ps[xp + row]), sp_of(ps[xm + row]), pn,
+                                                  pm, {u.x, u.y}, {uxm.x, uxm.y}, {u.z, u.w},
+                                                  {um.z, um.w});
+        const Sp<float> tv = diag * pc - 0.5f * o;
+        ts[x + row] = f4_of(tv);
+        pap += norm2(tv);
+        pm = pc;
+        pc = pn;
+        um = u;
+      }
+    }
+    const float papt = csum(pap, 0);  // its cluster barrier also publishes t
+    if (!(papt > 0.f) || !isfinite(papt)) {
+      flags |= 2;
+      break;
+    }
+    const float alpha = rr / papt;
+    float rn2 = 0.f;
+    {
+      Sp<float> tm = sp_of(at(ts, tp, t0 - 1, x)), tc = sp_of(ts[t0 * L + x]);
+      float4 um = at(Us, Up, t0 - 1, x);
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int row = (t0 + j) * L;
+        const Sp<float> tn = sp_of(at(ts, tp, t0 + j + 1, x));
+        const float4 u = Us[x + row];
+        const float4 uxm = Us[xm + row];
+        const Sp<float> o = hop_sum<true, float>(sp_of(ts[xp + row]), sp_of(ts[xm + row]), tn, tm,
+                                                 {u.x, u.y}, {uxm.x, uxm.y}, {u.z, u.w},
+                                                 {um.z, um.w});
+        const Sp<float> Ap = diag * tc - 0.5f * o;
+        xv[j] = xv[j] + alpha * sp_of(ps[x + row]);
+        rv[j] = rv[j] - alpha * Ap;
+        rn2 += norm2(rv[j]);
+        tm = tc;
+        tc = tn;
+        um = u;
+      }
+    }
+    const float rrn = csum(rn2, 1);
+    rr_prev = rr;
+    rr = rrn;
+    beta = rr / rr_prev;
+    ++it;
+    if (!isfinite(rr)) {
+      flags |= 2;
+      break;
+    }
+    rmax = fmaxf(rmax, rr);
+    if (rr <= tol2bb || rr < delta2 * rmax || it >= a.maxit) {
+      // reliable update on this half: x_hi += x; t64 = D x_hi; r = b - D^dag t64
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const long long n = base + x + (t0 + j) * L;
+        st_sp(a.x, n, ld_sp_cg(a.x, n) + to_dbl(xv[j]));
+        xv[j] = {{0.f, 0.f}, {0.f, 0.f}};
+      }
+      cl.sync();
+      const double dg = 2.0 + ci.m0;
+      const int lshift = (L & (L - 1)) == 0 ? __ffs(L) - 1 : -1;
+      for (int l = threadIdx.x; l < HV; l += NT) {
+        const Nb n = neighbours(l + (int)rank * HV, L, T, lshift);
+        st_sp(a.t64, ci.off + n.l, dslash_glob<false>(a.x, a.U64, ci.off, n, dg));
+      }
+      cl.sync();
+      double v = 0.0;
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int l = x + (t0 + j) * L + (int)rank * HV;
+        const Nb n = neighbours(l, L, T, lshift);
+        const Sp<double> r =
+            ld_sp(a.b, ci.off + l) - dslash_glob<true>(a.t64, a.U64, ci.off, n, dg);
+        v += norm2(r);
+        rv[j] = to_flt(r);
+      }
+      rr_true = csumd(v);
+      ++updates;
+      if (!isfinite(rr_true)) {
+        flags |= 2;
+        break;
+      }
+      if (rr_true <= a.tol2 * bb) break;
+      if (it >= a.maxit) {
+        flags |= 1;
+        break;
+      }
+      beta = (float)(rr_true / (double)rr_prev);
+      rr = (float)rr_true;
+      rmax = rr;
+    }
+  }
+  cl.sync();  // neither block leaves while the other may read its shared memory
+  if (threadIdx.x == 0 && rank == 0) {
+    CgChain* cc = a.cgc + c;
+    cc->bb = bb;
+    cc->rr = rr;
+    cc->rr_true = rr_true;
+    cc->iters = it;
+    cc->flags = flags;
+    cc->state = 0;
+    cc->need_update = updates;
+  }
+}
+
 // FP64: the same iteration with all fields in global memory (x is the output,
 // r64, p64, t64 scratch), one block per chain.
 __global__ void __launch_bounds__(kChainThreads, 1) k_cg_chain_f64(ChainCgArgs a) {
@@ -581,10 +788,12 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_cg_chain_f64(ChainCgArgs a
 // chain's shape to match).
 bool chain_variant_applies(const sm_lattice* L, int v) {
   if (v == 0) return true;
-  const int nt = v == 1 ? 512 : 256, rows = v == 1 ? 8 : 16;
-  if (v != 1 && v != 2) return false;
+  if (v < 0 || v > 3) return false;
+  // rows of the chain the column layout covers: 512 x 8, 256 x 16, and for
+  // the cluster form 256 x 8 per half
+  const int nt = v == 1 ? 512 : 256, rows = v == 2 ? 16 : 8, halves = v == 3 ? 2 : 1;
   for (const ChainInfo& ci : L->chains)
-    if (nt % ci.L != 0 || ci.T != rows * (nt / ci.L)) return false;
+    if (nt % ci.L != 0 || ci.T != halves * rows * (nt / ci.L)) return false;
   return true;
 }
 
@@ -628,7 +837,13 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
     };
     int v = L->cg_variant;
     if (v < 0 || !chain_variant_applies(L, v)) v = 0;
-    if (v == 1) {
+    if (v == 3) {
+      const size_t hs = smem / 2;  // each block holds half the chain
+      e = cudaFuncSetAttribute(k_cg_chain_cluster<8, 256>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs);
+      if (e == cudaSuccess)
+        k_cg_chain_cluster<8, 256><<<dim3(2 * L->nchains), dim3(256), hs, c.s>>>(a);
+    } else if (v == 1) {
       go(k_cg_chain_col<8, 512>, 512);
     } else if (v == 2) {
       go(k_cg_chain_col<16, 256>, 256);

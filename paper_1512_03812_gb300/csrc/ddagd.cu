@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kTX* kTY) k_ddagd_tile(const ChainInfo* __rest
 // every thread issues all of its 16-byte global -> shared copies before one
 // wait, so a block has its whole 42 KB region in flight.  Interior tiles
 // (whose region needs no periodic wrap) skip the wrap arithmetic.
-constexpr int kBX = 64, kBY = 16, kBT = 256;
+constexpr int kBX = 64, kBY = 16, kBT = 512;
 constexpr int kBPX = kBX + 4, kBPY = kBY + 4;
 constexpr int kBUX = kBX + 3, kBUY = kBY + 3;
 constexpr int kBDX = kBX + 2, kBDY = kBY + 2;
@@ -170,15 +170,38 @@ __global__ void __launch_bounds__(kBT) k_ddagd_tile_big(const ChainInfo* __restr
   const float2* su2 = reinterpret_cast<const float2*>(su);
   auto UX = [&](int u) { const float2 v = su2[2 * u]; return Cx<float>{v.x, v.y}; };
   auto UT = [&](int u) { const float2 v = su2[2 * u + 1]; return Cx<float>{v.x, v.y}; };
-  for (int i = tid; i < kBDX * kBDY; i += kBT) {
-    const int dy = i / kBDX, dx = i - dy * kBDX;
+  // t = D in on the (kBX + 2) x (kBY + 2) region.  Threads 0 .. 383 walk the
+  // 64 main columns in 6 strips of 3 rows (warps stay on one row: no bank
+  // conflicts; t-neighbours and U_t(n - t) come from registers); threads
+  // 384 .. 419 do the two halo columns site by site.
+  constexpr int kDRows = kBDY / 6;
+  auto dsite = [&](int dx, int dy, const Sp<float>& pm, const Sp<float>& pc,
+                   const Sp<float>& pn, Cx<float> utm) {
     const int p = (dy + 1) * kBPX + dx + 1, u = (dy + 1) * kBUX + dx + 1;
     const float4 uu = su[u];
-    const Sp<float> o = hop_sum<false, float>(S(sp[p + 1]), S(sp[p - 1]), S(sp[p + kBPX]),
-                                              S(sp[p - kBPX]), {uu.x, uu.y}, UX(u - 1),
-                                              {uu.z, uu.w}, UT(u - kBUX));
-    const Sp<float> tv = diag * S(sp[p]) - 0.5f * o;
-    st[i] = make_float4(tv.a.re, tv.a.im, tv.b.re, tv.b.im);
+    const Sp<float> o = hop_sum<false, float>(S(sp[p + 1]), S(sp[p - 1]), pn, pm, {uu.x, uu.y},
+                                              UX(u - 1), {uu.z, uu.w}, utm);
+    const Sp<float> tv = diag * pc - 0.5f * o;
+    st[dy * kBDX + dx] = make_float4(tv.a.re, tv.a.im, tv.b.re, tv.b.im);
+    return Cx<float>{uu.z, uu.w};
+  };
+  if (tid < 6 * kBX) {
+    const int dx = tid % kBX + 1, dy0 = (tid / kBX) * kDRows;
+    int p = (dy0 + 1) * kBPX + dx + 1;
+    Sp<float> pm = S(sp[p - kBPX]), pc = S(sp[p]);
+    Cx<float> utm = UT((dy0 + 1) * kBUX + dx + 1 - kBUX);
+#pragma unroll
+    for (int j = 0; j < kDRows; ++j, p += kBPX) {
+      const Sp<float> pn = S(sp[p + kBPX]);
+      utm = dsite(dx, dy0 + j, pm, pc, pn, utm);
+      pm = pc;
+      pc = pn;
+    }
+  } else if (tid < 6 * kBX + 2 * kBDY) {
+    const int k = tid - 6 * kBX;
+    const int dx = k < kBDY ? 0 : kBDX - 1, dy = k % kBDY;
+    const int p = (dy + 1) * kBPX + dx + 1, u = (dy + 1) * kBUX + dx + 1;
+    dsite(dx, dy, S(sp[p - kBPX]), S(sp[p]), S(sp[p + kBPX]), UT(u - kBUX));
   }
   __syncthreads();
 

@@ -127,7 +127,7 @@ int launch_ddagd(Ctx& c, const R* U, const R* in, R* out);
 // Chain-resident CG (cg_chain.cu): one block per chain.
 bool chain_cg_fits(const sm_lattice* L, int prec);
 bool chain_variant_applies(const sm_lattice* L, int v);
-constexpr int kChainVariants = 3;
+constexpr int kChainVariants = 4;
 int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
                     const sm_cg_params& cg);
 

@@ -477,6 +477,14 @@ int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, doubl
 
 using namespace sm;
 
+extern "C" int sm_set_cg_variant(sm_lattice* lat, int variant) {
+  if (!lat) return fail(SM_ERR_ARG, "sm_set_cg_variant: lattice is NULL");
+  if (variant != -1 && !chain_variant_applies(lat, variant))
+    return fail(SM_ERR_ARG, "sm_set_cg_variant: variant %d does not fit these chains", variant);
+  lat->cg_variant = variant;
+  return SM_OK;
+}
+
 extern "C" int sm_autotune_cg(sm_lattice* lat, const double* U64, const float* U32,
                               const double* b, double* x, const sm_cg_params* cg, void* ws,
                               size_t ws_bytes, int* variant, double* ms, void* stream) {

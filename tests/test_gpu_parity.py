@@ -152,6 +152,36 @@ def test_cg_layouts_agree(torch):
         assert rel_err(b.chain(xg, c), b.chain(xc, c)) < 1e-12
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_chain_cg_kernel_variants_64x64(torch, variant):
+    """Every kernel variant of the chain-resident mixed CG (strided, column
+    512x8, column 256x16, two-block cluster) on 64x64 chains: the FP64 true
+    residual meets the tolerance and x agrees with the FP64 solve; one
+    trajectory matches the oracle's Delta H and decision."""
+    import paper_1512_03812_gb300 as P
+    b = batch(torch, dims=[(64, 64)] * 3, betas=2.0, kappas=0.24, seed=9)
+    b.lat.set_cg_variant(variant)
+    q, phi = b.q(), b.spinor()
+    U64, U32 = b.lat.links(b.dev(q))
+    x64, _, _ = b.lat.cg_solve(U64, U32, b.dev(phi), cg(1e-12))
+    xm, iters, relres = b.lat.cg_solve(U64, U32, b.dev(phi),
+                                       P.CG(tol=1e-10, prec="mixed", delta=0.01, algo="chain"))
+    assert (relres <= 1e-10).all(), relres
+    r = b.dev(phi) - b.lat.apply_DdagD(U64, xm)
+    for c in range(3):
+        assert np.linalg.norm(b.chain(r, c)) <= 1.0000001e-10 * np.linalg.norm(b.chain(phi, c))
+        assert rel_err(b.chain(xm, c), b.chain(x64, c)) < 1e-8
+    p, eta = b.p(), b.eta()
+    md = P.MD(scheme="adapted_nested_fg", tau=0.25, n=1, M=2,
+              cg=P.CG(tol=1e-12, prec="mixed", delta=0.01, algo="chain"))
+    dH, H0, acc = b.lat.hmc_trajectory(b.dev(q), b.dev(p), b.dev(eta), 0.5, md)
+    ol = b.olat[0]
+    ro = ig.hmc_trajectory(ol, b.chain(q, 0), b.chain(p, 0), b.chain(eta, 0), 0.5,
+                           "adapted_nested_fg", 0.25, 1, M=2, solver=sw.Solver(1e-13))
+    assert abs(dH[0] - ro.dH) < 1e-6, (dH[0], ro.dH)
+    assert bool(acc[0]) == ro.accepted
+
+
 def test_chain_solver_rejects_oversized_chains(torch):
     import paper_1512_03812_gb300 as P
     b = batch(torch, dims=[(128, 64)])
