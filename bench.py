@@ -233,23 +233,42 @@ def run_ours(args):
 
     flush = torch.empty(int(256 * 2 ** 20), dtype=torch.uint8, device=dev)
 
-    def step(q, p, e, u):
-        flush.fill_(1)  # evict the previous step's working set from L2
-        return lat.hmc_trajectory(q, p, e, u, md, check=False)
-
     # pick the chain-resident CG kernel for this batch (untimed): time every
     # applicable variant on one representative solve at the start links
     tune = None
-    if args.prec == "mixed" and args.algo != "grid":
+    if args.cg_variant >= 0:
+        lat.set_cg_variant(args.cg_variant)
+        tune = {"variant": args.cg_variant, "pinned": True}
+    elif args.prec == "mixed" and args.algo != "grid":
         U64s, U32s = lat.links(q_start)
         b_t = torch.view_as_complex(torch.randn((N, 2, 2), generator=gen, device=dev,
                                                 dtype=torch.float64)).contiguous()
         v, vms = lat.autotune_cg(U64s, U32s, b_t, cgp)
         tune = {"variant": v, "ms_per_variant": [round(t, 3) for t in vms],
                 "variants": ["strided 512x8", "column 512x8", "column 256x16",
-                             "column 2-block cluster 256x8"]}
+                             "column 2-block cluster 256x8", "column 2-block cluster 512x4"]}
         log(f"autotuned chain CG: variant {v}, ms {vms}")
         del U64s, U32s, b_t
+
+    # (the graph keeps the kernel variants chosen when it is captured)
+    graph = None
+    if args.graph:
+        # one captured trajectory bound to fixed buffers; a step refills them
+        p_buf = torch.empty((N, 2), dtype=torch.float64, device=dev)
+        e_buf = torch.empty((N, 2), dtype=torch.complex128, device=dev)
+        q_buf = q_start.clone()
+        graph = lat.hmc_graph(q_buf, p_buf, e_buf, md)
+
+    def step(q, p, e, u):
+        flush.fill_(1)  # evict the previous step's working set from L2
+        if graph is None:
+            return lat.hmc_trajectory(q, p, e, u, md, check=False)
+        q_buf.copy_(q)
+        p_buf.copy_(p)
+        e_buf.copy_(e)
+        r = graph.run(u)
+        q.copy_(q_buf)
+        return r
 
     q = q_start.clone()
     pw, ew, uw = draws(args.warmup)
@@ -389,7 +408,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32+f64" if args.prec == "mixed" else "f64",
         "data": "synthetic (own thermalised start, seeded momenta/noise)",
         "config": dict(W, chains_per_gpu=B, precision=args.prec, parallelism=f"replicas{world}",
-                       l2="flushed between steps (256 MiB write)", cg_autotune=tune),
+                       l2="flushed between steps (256 MiB write)", cg_autotune=tune,
+                       cuda_graph=bool(args.graph)),
         "acceptance": round(acc_rate, 4),
         "e2e": {"value": round(aggregate(world, B, K, e2e_ms), 3), "unit": "trajectories/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -401,6 +421,121 @@ def run_ours(args):
         "cpu_baseline": cpu,
     }
     print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------- the other two configurations --
+
+OTHER_WORKLOADS = {
+    "batched": {
+        "workload": "256 chains, sides from {16,32,48,64,128}, beta in {1,2,4}, kappa in "
+                    "[0.20,0.26], adapted nested FG n=6 m=2, mixed CG tol 1e-10",
+        "chains": 256, "scheme": "adapted_nested_fg", "tau": 1.0, "n": 6, "M": 2,
+        "cg_tol": 1e-10, "cg_tol_action": 1e-12, "therm": (6, 4)},
+    "large": {
+        "workload": "2048x2048 beta=8.0 kappa=0.255, adapted nested FG n=8 m=3, mixed CG tol 1e-10",
+        "L": 2048, "beta": 8.0, "kappa": 0.255, "scheme": "adapted_nested_fg", "tau": 1.0,
+        "n": 8, "M": 3, "cg_tol": 1e-10, "cg_tol_action": 1e-12, "therm": (3, 2)},
+}
+
+
+def run_other(args):
+    """Trajectory throughput of the batched-chain or the large-lattice
+    configuration (one JSON line; thermalisation untimed, as for the
+    default workload)."""
+    import torch
+
+    import paper_1512_03812_gb300 as P
+    from paper_1512_03812_gb300 import binding
+    from paper_1512_03812_gb300 import inputs as I
+    spec = OTHER_WORKLOADS[args.workload]
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    P.build()
+    if args.workload == "batched":
+        n = spec["chains"]
+        sides = I.chain_sides(n, 81)
+        betas, kappas = I.chain_couplings(n, 82)
+        Ls = Ts = [int(s) for s in sides]
+    else:
+        Ls = Ts = [spec["L"]]
+        betas, kappas = np.array([spec["beta"]]), np.array([spec["kappa"]])
+    m0 = np.array([kappa_to_m0(k) for k in kappas])
+    lat = P.Lattice(Ls, Ts, betas, m0, device=dev)
+    N, B = lat.N, lat.nchains
+    g = torch.Generator(device=dev)
+    g.manual_seed(4321)
+
+    def draw():
+        p = torch.randn((N, 2), generator=g, device=dev, dtype=torch.float64)
+        e = torch.view_as_complex(torch.randn((N, 2, 2), generator=g, device=dev,
+                                              dtype=torch.float64) * math.sqrt(0.5)).contiguous()
+        u = torch.rand(B, generator=g, device=dev, dtype=torch.float64).cpu().numpy()
+        return p, e, u
+
+    fine = P.CG(1e-8, 50000, "mixed", delta=args.delta)
+    q = torch.zeros((N, 2), dtype=torch.float64, device=dev)
+    heavy = P.Lattice(Ls, Ts, betas, np.full(B, kappa_to_m0(0.10)), device=dev)
+    t0 = time.time()
+    for _ in range(spec["therm"][0]):
+        p, e, _ = draw()
+        heavy.hmc_trajectory(q, p, e, np.zeros(B),
+                             P.MD(scheme="nested_leapfrog", tau=1.0, n=5, M=8, cg=fine), check=False)
+    for _ in range(spec["therm"][1]):
+        p, e, _ = draw()
+        lat.hmc_trajectory(q, p, e, np.zeros(B),
+                           P.MD(scheme="nested_leapfrog", tau=1.0, n=16, M=4, cg=fine), check=False)
+    del heavy
+    log(f"{args.workload}: thermalised in {time.time() - t0:.1f}s")
+    cgp = P.CG(tol=spec["cg_tol"], maxit=50000, prec="mixed", delta=args.delta, algo=args.algo)
+    md = P.MD(scheme=spec["scheme"], tau=spec["tau"], n=spec["n"], M=spec["M"], cg=cgp,
+              tol_action=spec["cg_tol_action"])
+    flush = torch.empty(int(256 * 2 ** 20), dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        p, e, u = draw()
+        flush.fill_(1)
+        lat.hmc_trajectory(q, p, e, u, md, check=False)
+    draws = [draw() for _ in range(args.steps)]
+    binding.profile_enable(True)
+    binding.profile_read(reset=True)
+    n0 = binding.launch_count()
+    clocks = Clocks(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    accs = []
+    for p, e, u in draws:
+        flush.fill_(1)
+        _, _, acc = lat.hmc_trajectory(q, p, e, u, md, check=False)
+        accs.append(acc)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    prof = binding.profile_read(reset=True)
+    binding.profile_enable(False)
+    st = lat.stats.as_dict()
+    peaks, src = measured_peaks()
+    ksec = prof["iter_ms"] / 1e3
+    bps = CG_BYTES_PER_SITE_ITER["mixed"]
+    ach = bps * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
+    print(json.dumps({
+        "metric": "HMC trajectories/s", "value": round(B * args.steps / (ms / 1e3), 4),
+        "unit": "trajectories/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (own thermalised start)",
+        "config": dict({k: v for k, v in spec.items() if k != "therm"}, sites=N, chains=B,
+                       cg_delta=args.delta, l2="flushed between steps (256 MiB write)"),
+        "acceptance": round(float(np.mean(np.concatenate(accs))), 4),
+        "last_step_stats": st, "gpu_launches": int(binding.launch_count() - n0),
+        "roofline": {"bound": "hbm", "kernel": "cg iteration (grid-wide k_cg_a + k_cg_b)",
+                     "achieved": round(ach, 1), "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                     "frac": round(ach / float(peaks["hbm_gbs"]), 4), "peak_source": src,
+                     "bytes_per_site_iter": bps, "site_iters": prof["site_iters"],
+                     "kernel_ms": round(prof["iter_ms"], 2), "res_ms": round(prof["res_ms"], 2),
+                     "kernel_share_of_step": round(prof["iter_ms"] / ms, 4), "traffic": None},
+        "clocks": clk}), flush=True)
 
 
 # ------------------------------------------------- D^dag D at 2048 x 2048 --
@@ -500,6 +635,10 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ddagd", action="store_true")
+    ap.add_argument("--cg-variant", type=int, default=-1)
+    ap.add_argument("--graph", action="store_true",
+                    help="replay one captured trajectory (CUDA graph) per step")
+    ap.add_argument("--workload", default="default", choices=["default", "batched", "large"])
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])
     ap.add_argument("--M", type=int, default=WORKLOAD["M"])
     ap.add_argument("--delta", type=float, default=0.01)
@@ -507,6 +646,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "default":
+        run_other(args)
     else:
         run_ours(args)
 

@@ -170,6 +170,11 @@ int sm_profile_read(double* iter_ms, double* res_ms, long long* batched_iters,
 int sm_lattice_create(int nchains, const int* L, const int* T, const double* beta,
                       const double* m0, sm_lattice** out);
 int sm_lattice_destroy(sm_lattice* lat);
+/* Reads and clears the lattice's device error word after synchronising the
+ * device: nonzero (and SM_ERR_TIMEOUT) if a bounded device-side wait of a
+ * kernel on this lattice gave up since the last check (for example a TMA copy
+ * that did not complete; the affected tile was not computed). */
+int sm_lattice_check(const sm_lattice* lat, int* code);
 /* Total number of sites N of the batch. */
 long long sm_lattice_sites(const sm_lattice* lat);
 int sm_lattice_chains(const sm_lattice* lat);
@@ -240,11 +245,11 @@ int sm_cg_solve(const sm_lattice* lat, const double* U64, const float* U32, cons
  * any chain up to 4096 sites; 1: column layout, 512 threads x 8 rows; 2:
  * column layout, 256 threads x 16 rows; 3: column layout split over a
  * cluster of two blocks, 256 threads x 8 rows each, rows exchanged through
- * distributed shared memory) on the given solve (b, FP64; x is overwritten),
- * and stores the fastest in the lattice object, which later SM_MIXED
- * chain-resident solves use.  variant (host, may be NULL) receives the
- * choice, ms (host [4], may be NULL) each variant's time or -1 where it does
- * not apply.  The variants differ only in their reduction order: results
+ * distributed shared memory; 4: the same with 512 threads x 4 rows, one
+ * block per SM) on the given solve (b, FP64; x is overwritten), and stores
+ * the fastest in the lattice object, which later SM_MIXED chain-resident
+ * solves use.  variant (host, may be NULL) receives the choice, ms (host [5],
+ * may be NULL) each variant's time or -1 where it does not apply.  The variants differ only in their reduction order: results
  * agree to rounding, and a lattice object gives reproducible results once
  * tuned.  Needs SM_MIXED and chains of at most 4096 sites.  Synchronises. */
 int sm_autotune_cg(sm_lattice* lat, const double* U64, const float* U32, const double* b,
@@ -334,6 +339,33 @@ int sm_hmc_trajectory(const sm_lattice* lat, double* q, const double* p0, const 
                       const double* u, const sm_md_params* md, void* ws, size_t ws_bytes,
                       double* dH, double* H0, int* accepted, double* p_out, double* q_md,
                       sm_stats* stats, void* stream);
+
+/* ------------------------------------------------ captured trajectories ---- */
+
+/* One HMC update of every chain captured as a CUDA graph (Sec. 2.1, the same
+ * computation as sm_hmc_trajectory): the device part -- heatbath, H at the
+ * start, the MD trajectory, H at the end -- is recorded once on `stream` (a
+ * non-default stream) and replayed by sm_hmc_graph_run; the Metropolis
+ * decisions and the restoring of rejected chains follow each replay on the
+ * host.  The graph is bound to the buffers given here: q (device, updated in
+ * place by every run), p0 and eta (device; refill them between runs), ws,
+ * and to md.  Every CG solve must be chain-resident (SM_CG_AUTO or
+ * SM_CG_CHAIN, chains that fit): their per-chain outcomes stay on the device
+ * until the end of a run.  Capture runs nothing.  The buffers and the lattice
+ * must outlive the graph, and runs on one graph (or anything else using its
+ * workspace) must not overlap.  The graph keeps the CG kernel variant the
+ * lattice had when it was captured (tune with sm_autotune_cg first).  CG
+ * kernel timing (sm_profile_enable) does not see solves inside a graph. */
+typedef struct sm_hmc_graph sm_hmc_graph;
+int sm_hmc_graph_create(const sm_lattice* lat, double* q, const double* p0, const double* eta,
+                        const sm_md_params* md, void* ws, size_t ws_bytes, sm_hmc_graph** out,
+                        void* stream);
+/* Replays the captured trajectory and takes the Metropolis decisions as
+ * sm_hmc_trajectory does (u, dH, H0, accepted host arrays [nchains]).
+ * Synchronises. */
+int sm_hmc_graph_run(sm_hmc_graph* g, const double* u, double* dH, double* H0, int* accepted,
+                     sm_stats* stats, void* stream);
+int sm_hmc_graph_destroy(sm_hmc_graph* g);
 
 #ifdef __cplusplus
 }

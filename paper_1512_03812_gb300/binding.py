@@ -83,6 +83,7 @@ _SIGS = {
     "sm_lattice_create": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     "sm_lattice_destroy": (ctypes.c_int, [_P]),
     "sm_lattice_sites": (ctypes.c_longlong, [_P]),
+    "sm_lattice_check": (ctypes.c_int, [_P, _P]),
     "sm_lattice_chains": (ctypes.c_int, [_P]),
     "sm_workspace_bytes": (ctypes.c_size_t, [_P]),
     "sm_links": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -113,6 +114,10 @@ _SIGS = {
                                         ctypes.c_size_t, ctypes.POINTER(Stats), _P]),
     "sm_md_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(MdParams), ctypes.c_double, _P,
                                   ctypes.c_size_t, ctypes.POINTER(Stats), _P]),
+    "sm_hmc_graph_create": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(MdParams), _P,
+                                           ctypes.c_size_t, ctypes.POINTER(_P), _P]),
+    "sm_hmc_graph_run": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
+    "sm_hmc_graph_destroy": (ctypes.c_int, [_P]),
     "sm_hmc_trajectory": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(MdParams), _P,
                                          ctypes.c_size_t, _P, _P, _P, _P, _P,
                                          ctypes.POINTER(Stats), _P]),
@@ -227,6 +232,13 @@ class Lattice:
             _LIB.sm_lattice_destroy(self._h)
             self._h = None
 
+    def check(self) -> int:
+        """Device-side error word of this lattice (0: none), cleared; raises
+        SchwingerError if a bounded device wait gave up."""
+        code = ctypes.c_int()
+        _check(_LIB.sm_lattice_check(self._h, ctypes.byref(code)))
+        return code.value
+
     # ---------------------------------------------------------- helpers --
     def field(self, dtype=torch.float64):
         return torch.empty((self.N, 2), dtype=dtype, device=self.device)
@@ -271,12 +283,17 @@ class Lattice:
         (variant, [ms per variant or -1])."""
         x = torch.empty_like(b)
         v = ctypes.c_int()
-        ms = np.zeros(4)
+        ms = np.zeros(5)
         p = cg.c()
         _check(_LIB.sm_autotune_cg(self._h, _ptr(U64), _ptr(U32), _ptr(b), _ptr(x),
                                    ctypes.byref(p), *self._ws(), ctypes.byref(v), ms.ctypes.data,
                                    _stream()))
         return v.value, ms.tolist()
+
+    def hmc_graph(self, q, p0, eta, md: MD, stream=None) -> "HmcGraph":
+        """Captures one HMC trajectory of every chain as a CUDA graph bound to
+        these tensors (see HmcGraph)."""
+        return HmcGraph(self, q, p0, eta, md, stream)
 
     def set_cg_variant(self, variant: int):
         """Pins the chain-resident mixed CG kernel variant (-1: default)."""
@@ -360,6 +377,42 @@ class Lattice:
         if check or rc not in (SM_ERR_NAN, SM_ERR_NOT_CONVERGED):
             _check(rc)
         return dH, H0, acc.astype(bool)
+
+
+class HmcGraph:
+    """A captured HMC trajectory of a lattice batch (sm_hmc_graph_*): bound to
+    the tensors q (updated in place), p0 and eta (refill between runs)."""
+
+    def __init__(self, lat: "Lattice", q, p0, eta, md: MD, stream=None):
+        self.lat, self.q, self.p0, self.eta = lat, q, p0, eta  # keep the buffers alive
+        self.stream = stream or torch.cuda.Stream(device=lat.device)
+        self._m = md.c()
+        h = _P()
+        torch.cuda.current_stream(lat.device).synchronize()
+        _check(_LIB.sm_hmc_graph_create(lat._h, _ptr(q), _ptr(p0), _ptr(eta), ctypes.byref(self._m),
+                                        *lat._ws(), ctypes.byref(h), self.stream.cuda_stream))
+        self._h = h
+
+    def run(self, u):
+        """Replays the trajectory; returns (dH, H0, accepted) like
+        Lattice.hmc_trajectory(check=False)."""
+        n = self.lat.nchains
+        u = np.ascontiguousarray(np.broadcast_to(np.asarray(u, dtype=np.float64), (n,)))
+        dH, H0 = np.zeros(n), np.zeros(n)
+        acc = np.zeros(n, dtype=np.int32)
+        self.stream.wait_stream(torch.cuda.current_stream(self.lat.device))
+        rc = _LIB.sm_hmc_graph_run(self._h, u.ctypes.data, dH.ctypes.data, H0.ctypes.data,
+                                   acc.ctypes.data, ctypes.byref(self.lat.stats),
+                                   self.stream.cuda_stream)
+        torch.cuda.current_stream(self.lat.device).wait_stream(self.stream)
+        if rc not in (SM_ERR_NAN, SM_ERR_NOT_CONVERGED):
+            _check(rc)
+        return dH, H0, acc.astype(bool)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _LIB is not None:
+            _LIB.sm_hmc_graph_destroy(self._h)
+            self._h = None
 
 
 def apply_DdagD_noalloc(L: int, T: int, m0: float, U, psi, out=None):

@@ -22,6 +22,8 @@
 namespace sm {
 
 constexpr int kChainThreads = 1024;
+// Largest chain volume the shared-memory FP32 form holds (48 B per site).
+constexpr int kChainMaxVolume = 4096;
 
 struct ChainCgArgs {
   const ChainInfo* chains;
@@ -497,19 +499,19 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_col(ChainCgArgs a) {
   }
 }
 
-// The column layout split over a cluster of two blocks: block rank k owns the
-// rows [k T/2, (k+1) T/2) of the chain (U, p, t of those rows in its shared
-// memory: 96 KB at 64 x 64, so two blocks fit on one SM and 200 chains fill
-// 152 SMs in about 1.5 waves instead of 2).  The rows just below and above
-// a block's half are read from the other block's shared memory (distributed
-// shared memory), and block sums are combined through it.  Every decision is
-// taken on sums that both blocks add in the same order (rank 0's part plus
-// rank 1's part), so both execute the same sequence of cluster barriers; a
-// final barrier keeps either block from exiting while the other may still
-// read its shared memory.
-template <int R, int NT>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT, 2)
-    k_cg_chain_cluster(ChainCgArgs a) {
+// The column layout split over a cluster of K blocks: block rank k owns the
+// rows [k T/K, (k+1) T/K) of the chain (U, p, t of those rows in its shared
+// memory).  K = 2 at 64 x 64 (96 KB per block, two blocks per SM); K = 4 at
+// 128 x 128 (192 KB per block), which keeps such chains chain-resident.  The
+// row just below a block's part is read from rank k - 1's shared memory and
+// the row just above from rank k + 1's (distributed shared memory; ranks wrap
+// around with the lattice), and block sums are combined through it.  Every
+// decision is taken on sums that all blocks add in the same order (rank 0's
+// part first), so all execute the same sequence of cluster barriers; a final
+// barrier keeps a block from exiting while another may still read its shared
+// memory.
+template <int R, int NT, int K>
+__global__ void __launch_bounds__(NT, (K == 2 && NT == 256 ? 2 : 1)) k_cg_chain_cluster(ChainCgArgs a) {
   namespace cgr = cooperative_groups;
   cgr::cluster_group cl = cgr::this_cluster();
   extern __shared__ float4 smem[];
@@ -518,27 +520,40 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT, 2)
   __shared__ float slot[2];   // this block's part of the two sums of an iteration
   __shared__ double slotd;    // this block's part of an FP64 sum
   const unsigned rank = cl.block_rank();
-  const int c = a.list[blockIdx.x >> 1];
+  const unsigned rb = (rank + K - 1) % K, ra = (rank + 1) % K;  // ranks below and above
+  const int c = a.list[blockIdx.x / K];
   const ChainInfo ci = a.chains[c];
-  const int L = ci.L, T = ci.T, H = T / 2, HV = H * L;
-  const long long base = ci.off + (long long)rank * HV;  // first global site of this half
+  const int L = ci.L, T = ci.T, H = T / K, HV = H * L;
+  const long long base = ci.off + (long long)rank * HV;  // first global site of this part
   float4* Us = smem;
   float4* ps = smem + HV;
   float4* ts = smem + 2 * HV;
-  float4* Up = cl.map_shared_rank(Us, rank ^ 1);
-  float4* pp = cl.map_shared_rank(ps, rank ^ 1);
-  float4* tp = cl.map_shared_rank(ts, rank ^ 1);
-  float* slot0 = cl.map_shared_rank(slot, 0);
-  float* slot1 = cl.map_shared_rank(slot, 1);
-  double* slotd0 = cl.map_shared_rank(&slotd, 0);
-  double* slotd1 = cl.map_shared_rank(&slotd, 1);
+  const float4* Ub = cl.map_shared_rank(Us, rb);
+  const float4* pb = cl.map_shared_rank(ps, rb);
+  const float4* tb = cl.map_shared_rank(ts, rb);
+  const float4* Ua = cl.map_shared_rank(Us, ra);
+  const float4* pa = cl.map_shared_rank(ps, ra);
+  const float4* ta = cl.map_shared_rank(ts, ra);
   const float diag = (float)(2.0 + ci.m0);
   const int x = threadIdx.x % L, t0 = (threadIdx.x / L) * R;  // local rows t0 .. t0 + R - 1
   const int xp = x + 1 == L ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  // local row -1 is the other half's last row, local row H its first row
-  auto at = [&](const float4* own, const float4* peer, int lr, int xx) {
-    return lr < 0 ? peer[(H - 1) * L + xx] : (lr >= H ? peer[xx] : own[lr * L + xx]);
+  // local row -1 is the last row of the part below, local row H the first
+  // row of the part above
+  auto at = [&](const float4* own, const float4* below, const float4* above, int lr, int xx) {
+    return lr < 0 ? below[(H - 1) * L + xx] : (lr >= H ? above[xx] : own[lr * L + xx]);
+  };
+  auto ksum = [&](const float* s, int k) {
+    float tot = 0.f;
+#pragma unroll
+    for (int j = 0; j < K; ++j) tot += cl.map_shared_rank(const_cast<float*>(s), j)[k];
+    return tot;
+  };
+  auto ksumd = [&]() {
+    double tot = 0.0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) tot += *cl.map_shared_rank(&slotd, j);
+    return tot;
   };
   // block sum (FP32, finished by every warp), then the cluster sum
   auto csum = [&](float v, int k) {
@@ -551,14 +566,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT, 2)
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (threadIdx.x == 0) slot[k] = s;
     cl.sync();
-    return slot0[k] + slot1[k];
+    return ksum(slot, k);
   };
   auto csumd = [&](double v) {
     const double s = cta_sum(v, redd);
     if (threadIdx.x == 0) slotd = s;
     cl.sync();
-    const double tot = *slotd0 + *slotd1;
-    cl.sync();  // both have read before slotd is written again
+    const double tot = ksumd();
+    cl.sync();  // all have read before slotd is written again
     return tot;
   };
 
@@ -591,12 +606,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT, 2)
     cl.sync();  // both halves' p (and, first time round, U) are written
     float pap = 0.f;
     {
-      Sp<float> pm = sp_of(at(ps, pp, t0 - 1, x)), pc = sp_of(ps[t0 * L + x]);
-      float4 um = at(Us, Up, t0 - 1, x);
+      Sp<float> pm = sp_of(at(ps, pb, pa, t0 - 1, x)), pc = sp_of(ps[t0 * L + x]);
+      float4 um = at(Us, Ub, Ua, t0 - 1, x);
 #pragma unroll
       for (int j = 0; j < R; ++j) {
         const int row = (t0 + j) * L;
-        const Sp<float> pn = sp_of(at(ps, pp, t0 + j + 1, x));
+        const Sp<float> pn = sp_of(at(ps, pb, pa, t0 + j + 1, x));
         const float4 u = Us[x + row];
         const float4 uxm = Us[xm + row];
         const Sp<float> o = hop_sum<false, float>(sp_of(ps[xp + row]), sp_of(ps[xm + row]), pn,
@@ -618,12 +633,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT, 2)
     const float alpha = rr / papt;
     float rn2 = 0.f;
     {
-      Sp<float> tm = sp_of(at(ts, tp, t0 - 1, x)), tc = sp_of(ts[t0 * L + x]);
-      float4 um = at(Us, Up, t0 - 1, x);
+      Sp<float> tm = sp_of(at(ts, tb, ta, t0 - 1, x)), tc = sp_of(ts[t0 * L + x]);
+      float4 um = at(Us, Ub, Ua, t0 - 1, x);
 #pragma unroll
       for (int j = 0; j < R; ++j) {
         const int row = (t0 + j) * L;
-        const Sp<float> tn = sp_of(at(ts, tp, t0 + j + 1, x));
+        const Sp<float> tn = sp_of(at(ts, tb, ta, t0 + j + 1, x));
         const float4 u = Us[x + row];
         const float4 uxm = Us[xm + row];
         const Sp<float> o = hop_sum<true, float>(sp_of(ts[xp + row]), sp_of(ts[xm + row]), tn, tm,
@@ -690,7 +705,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT, 2)
       rmax = rr;
     }
   }
-  cl.sync();  // neither block leaves while the other may read its shared memory
+  cl.sync();  // no block leaves while another may read its shared memory
   if (threadIdx.x == 0 && rank == 0) {
     CgChain* cc = a.cgc + c;
     cc->bb = bb;
@@ -788,23 +803,138 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_cg_chain_f64(ChainCgArgs a
 // chain's shape to match).
 bool chain_variant_applies(const sm_lattice* L, int v) {
   if (v == 0) return true;
-  if (v < 0 || v > 3) return false;
+  if (v < 0 || v > 4) return false;
   // rows of the chain the column layout covers: 512 x 8, 256 x 16, and for
-  // the cluster form 256 x 8 per half
-  const int nt = v == 1 ? 512 : 256, rows = v == 2 ? 16 : 8, halves = v == 3 ? 2 : 1;
+  // the cluster forms 256 x 8 and 512 x 4 per half
+  const int nt = (v == 1 || v == 4) ? 512 : 256, rows = v == 2 ? 16 : (v == 4 ? 4 : 8),
+            halves = v >= 3 ? 2 : 1;
   for (const ChainInfo& ci : L->chains)
     if (nt % ci.L != 0 || ci.T != halves * rows * (nt / ci.L)) return false;
   return true;
 }
 
-// Largest chain volume the shared-memory FP32 form holds (48 B per site).
-constexpr int kChainMaxVolume = 4096;
+
+// A chain the 4-block cluster kernel holds: 512 threads per block walk 8-row
+// column strips, so L divides 512 and each block owns 8 * 512 / L rows.
+bool big_chain_shape(const ChainInfo& ci) {
+  return ci.L * ci.T > kChainMaxVolume && 512 % ci.L == 0 && ci.T == 4 * 8 * (512 / ci.L);
+}
 
 bool chain_cg_fits(const sm_lattice* L, int prec) {
   int vmax = 0;
-  for (const ChainInfo& ci : L->chains) vmax = ci.L * ci.T > vmax ? ci.L * ci.T : vmax;
-  if (prec == SM_MIXED) return vmax <= kChainMaxVolume;
+  bool all = true;
+  for (const ChainInfo& ci : L->chains) {
+    vmax = ci.L * ci.T > vmax ? ci.L * ci.T : vmax;
+    all = all && (ci.L * ci.T <= kChainMaxVolume || big_chain_shape(ci));
+  }
+  if (prec == SM_MIXED) return all;
   return vmax <= 4 * kChainMaxVolume;
+}
+
+// Launches a K-block-cluster chain kernel: nch chains, K blocks each.
+template <int K, typename Kern>
+static cudaError_t launch_cluster(Kern kern, int nch, int nt, size_t smem, cudaStream_t s,
+                                  const ChainCgArgs& a) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(K * nch));
+  cfg.blockDim = dim3((unsigned)nt);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = K;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+int chain_cg_prepare(const sm_lattice* L, const sm_cg_params& cg) {
+  if (cg.prec != SM_MIXED) return SM_OK;
+  int vmax = 0;
+  for (const ChainInfo& ci : L->chains) vmax = ci.L * ci.T > vmax ? ci.L * ci.T : vmax;
+  const int smem = 3 * vmax * (int)sizeof(float4);
+  cudaError_t e = cudaFuncSetAttribute(k_cg_chain_cluster<8, 256, 2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem / 2);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_chain_cluster<4, 512, 2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem / 2);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_chain_cluster<8, 512, 4>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 4096 * 16);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_chain_col<8, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_chain_col<16, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_chain_mixed<1, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_chain_mixed<2, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_chain_mixed<8, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return fail(SM_ERR_CUDA, "chain CG attributes: %s", cudaGetErrorString(e));
+  return SM_OK;
+}
+
+bool chain_cg_selected(const sm_lattice* L, const sm_cg_params& cg) {
+  const bool fits = chain_cg_fits(L, cg.prec);
+  return cg.algo == SM_CG_CHAIN ? fits : (cg.algo == SM_CG_AUTO && fits);
+}
+
+// Deferred mode: acc[c] |= flags, acc[nchains + c] += iterations.
+__global__ void k_cg_accumulate(const CgChain* __restrict__ cgc, int* acc, int nchains) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nchains) return;
+  acc[c] |= cgc[c].flags;
+  acc[nchains + c] += cgc[c].iters;
+}
+
+int chain_cg_accumulate(Ctx& c) {
+  const int n = c.L->nchains;
+  k_cg_accumulate<<<(n + 255) / 256, 256, 0, c.s>>>(c.w.cgc, c.w.acc, n);
+  return launched(c.st, "cg_accumulate");
+}
+
+// The chains of a mixed batch that fit the shared-memory form, solved by the
+// strided kernel (one block each) on c.s; the other chains are untouched.
+int chain_cg_launch_list(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
+                         const sm_cg_params& cg) {
+  const sm_lattice* L = c.L;
+  ChainCgArgs a{};
+  a.chains = L->d_chains;
+  a.list = L->d_small_list;
+  a.U32 = U32;
+  a.U64 = U64;
+  a.b = b;
+  a.x = x;
+  a.t64 = c.w.t;
+  a.r64 = c.w.r;
+  a.p64 = c.w.p0;
+  a.cgc = c.w.cgc;
+  a.tol2 = cg.tol * cg.tol;
+  a.delta2 = cg.delta * cg.delta;
+  a.maxit = cg.maxit;
+  int vmax = 0;
+  for (const ChainInfo& ci : L->chains)
+    if (ci.L * ci.T <= kChainMaxVolume && ci.L * ci.T > vmax) vmax = ci.L * ci.T;
+  const size_t smem = (size_t)3 * vmax * sizeof(float4);
+  const dim3 grid((unsigned)L->nsmall);
+  cudaError_t e = cudaSuccess;
+  auto go = [&](auto kern, int nt) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) kern<<<grid, dim3(nt), smem, c.s>>>(a);
+  };
+  if (vmax <= 1024)
+    go(k_cg_chain_mixed<1, 1024>, 1024);
+  else if (vmax <= 2048)
+    go(k_cg_chain_mixed<2, 1024>, 1024);
+  else
+    go(k_cg_chain_mixed<8, 512>, 512);
+  if (e != cudaSuccess) return fail(SM_ERR_CUDA, "chain CG attribute: %s", cudaGetErrorString(e));
+  return launched(c.st, "cg_chain_mixed_list");
 }
 
 int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
@@ -826,6 +956,28 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
   a.maxit = cg.maxit;
   const dim3 grid((unsigned)L->nchains), block(kChainThreads);
   (void)block;
+  if (cg.prec == SM_MIXED && L->nbig > 0) {
+    // small chains on the side stream, 4-block clusters for the large ones
+    cudaError_t e = cudaEventRecord(L->ev_fork, c.s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(L->side, L->ev_fork, 0);
+    if (e != cudaSuccess) return fail(SM_ERR_CUDA, "chain CG fork: %s", cudaGetErrorString(e));
+    int rc = SM_OK;
+    if (L->nbig < L->nchains) {
+      Ctx cs = c;
+      cs.s = L->side;
+      if ((rc = chain_cg_launch_list(cs, U64, U32, b, x, cg))) return rc;
+    }
+    ChainCgArgs ab = a;
+    ab.list = L->d_big_list;
+    e = launch_cluster<4>(k_cg_chain_cluster<8, 512, 4>, L->nbig, 512, (size_t)3 * 4096 * 16,
+                          c.s, ab);
+    if (e != cudaSuccess) return fail(SM_ERR_CUDA, "chain CG (clusters): %s", cudaGetErrorString(e));
+    if ((rc = launched(c.st, "cg_chain_cluster4"))) return rc;
+    e = cudaEventRecord(L->ev_join, L->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c.s, L->ev_join, 0);
+    if (e != cudaSuccess) return fail(SM_ERR_CUDA, "chain CG join: %s", cudaGetErrorString(e));
+    return SM_OK;
+  }
   if (cg.prec == SM_MIXED) {
     int vmax = 0;
     for (const ChainInfo& ci : L->chains) vmax = ci.L * ci.T > vmax ? ci.L * ci.T : vmax;
@@ -838,11 +990,9 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
     int v = L->cg_variant;
     if (v < 0 || !chain_variant_applies(L, v)) v = 0;
     if (v == 3) {
-      const size_t hs = smem / 2;  // each block holds half the chain
-      e = cudaFuncSetAttribute(k_cg_chain_cluster<8, 256>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs);
-      if (e == cudaSuccess)
-        k_cg_chain_cluster<8, 256><<<dim3(2 * L->nchains), dim3(256), hs, c.s>>>(a);
+      e = launch_cluster<2>(k_cg_chain_cluster<8, 256, 2>, L->nchains, 256, smem / 2, c.s, a);
+    } else if (v == 4) {
+      e = launch_cluster<2>(k_cg_chain_cluster<4, 512, 2>, L->nchains, 512, smem / 2, c.s, a);
     } else if (v == 1) {
       go(k_cg_chain_col<8, 512>, 512);
     } else if (v == 2) {

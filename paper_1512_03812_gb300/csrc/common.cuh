@@ -19,7 +19,8 @@ constexpr int kBlock = 256;  // threads per site block, one site per thread
 struct ChainInfo {
   int L, T;
   long long off;
-  int blk0, nblk;
+  int blk0, nblk;  // site blocks of the chain
+  int tb0, ntb;    // its tiles in the 64 x 16 tile table
   double beta, m0;
 };
 

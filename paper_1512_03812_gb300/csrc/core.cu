@@ -26,6 +26,8 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 int launched(sm_stats* st, const char* what) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (st) st->kernel_launches++;
@@ -57,6 +59,7 @@ size_t Ws::bytes(const sm_lattice* L) {
   b += align256(nc * sizeof(CgChain));
   b += align256(8 * nc * sizeof(double));
   b += align256(nc * sizeof(int));
+  b += align256(2 * nc * sizeof(int));
   b += align256(sizeof(int));
   return b;
 }
@@ -88,6 +91,7 @@ int Ws::carve(const sm_lattice* L, void* ws, size_t nbytes) {
   cgc = reinterpret_cast<CgChain*>(take(nc * sizeof(CgChain)));
   out = reinterpret_cast<double*>(take(8 * nc * sizeof(double)));
   flags = reinterpret_cast<int*>(take(nc * sizeof(int)));
+  acc = reinterpret_cast<int*>(take(2 * nc * sizeof(int)));
   n_active = reinterpret_cast<int*>(take(sizeof(int)));
   h_n_active = L->h_pinned;
   return SM_OK;
@@ -538,6 +542,7 @@ int sm_lattice_create(int nchains, const int* L, const int* T, const double* bet
   }
   lat->N = off;
   lat->nblocks = blk;
+  big_tile_ranges(lat);
   lat->cg_variant = -1;
   cudaGetDevice(&lat->device);
   cudaError_t e = cudaMalloc(&lat->d_chains, sizeof(ChainInfo) * nchains);
@@ -565,6 +570,38 @@ int sm_lattice_create(int nchains, const int* L, const int* T, const double* bet
     sm_lattice_destroy(lat);
     return rc;
   }
+  // mixed batches: which chains fit the chain-resident kernel, which the
+  // 4-block cluster kernel, and which take the grid-wide path
+  std::vector<int> small, big;
+  lat->grid_mask.assign(nchains, 1);
+  for (int c = 0; c < nchains; ++c) {
+    if (lat->chains[c].L * lat->chains[c].T <= 4096) {
+      small.push_back(c);
+      lat->grid_mask[c] = 0;
+    } else if (big_chain_shape(lat->chains[c])) {
+      big.push_back(c);
+    }
+  }
+  lat->nsmall = (small.size() < (size_t)nchains) ? (int)small.size() : 0;
+  lat->nbig = (small.size() + big.size() == (size_t)nchains) ? (int)big.size() : 0;
+  e = cudaMalloc(&lat->d_big_list, sizeof(int) * (big.empty() ? 1 : big.size()));
+  if (e == cudaSuccess && !big.empty())
+    e = cudaMemcpy(lat->d_big_list, big.data(), sizeof(int) * big.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&lat->d_grid_mask, nchains);
+  if (e == cudaSuccess) e = cudaMalloc(&lat->d_small_list, sizeof(int) * (small.empty() ? 1 : small.size()));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(lat->d_grid_mask, lat->grid_mask.data(), nchains, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !small.empty())
+    e = cudaMemcpy(lat->d_small_list, small.data(), sizeof(int) * small.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&lat->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(lat->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&lat->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lat->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lat->ev_join, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    sm_lattice_destroy(lat);
+    return fail(SM_ERR_CUDA, "lattice tables: %s", cudaGetErrorString(e));
+  }
   *out = lat;
   return SM_OK;
 }
@@ -575,6 +612,13 @@ int sm_lattice_destroy(sm_lattice* lat) {
   if (lat->d_blk_chain) cudaFree(lat->d_blk_chain);
   if (lat->d_chain_list) cudaFree(lat->d_chain_list);
   if (lat->d_tiles) cudaFree(lat->d_tiles);
+  if (lat->d_grid_mask) cudaFree(lat->d_grid_mask);
+  if (lat->d_err) cudaFree(lat->d_err);
+  if (lat->d_small_list) cudaFree(lat->d_small_list);
+  if (lat->d_big_list) cudaFree(lat->d_big_list);
+  if (lat->side) cudaStreamDestroy(lat->side);
+  if (lat->ev_fork) cudaEventDestroy(lat->ev_fork);
+  if (lat->ev_join) cudaEventDestroy(lat->ev_join);
   if (lat->d_tiles_big) cudaFree(lat->d_tiles_big);
   if (lat->h_pinned) cudaFreeHost(lat->h_pinned);
   if (lat->ev[0]) cudaEventDestroy(lat->ev[0]);
@@ -584,6 +628,18 @@ int sm_lattice_destroy(sm_lattice* lat) {
 }
 
 long long sm_lattice_sites(const sm_lattice* lat) { return lat ? lat->N : 0; }
+
+int sm_lattice_check(const sm_lattice* lat, int* code) {
+  if (!lat || !code) return fail(SM_ERR_ARG, "sm_lattice_check: NULL argument");
+  int h = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&h, lat->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(lat->d_err, 0, sizeof(int));
+  if (e != cudaSuccess) return fail(SM_ERR_CUDA, "sm_lattice_check: %s", cudaGetErrorString(e));
+  *code = h;
+  if (h) return fail(SM_ERR_TIMEOUT, "a bounded device-side wait gave up (code %d)", h);
+  return SM_OK;
+}
 int sm_lattice_chains(const sm_lattice* lat) { return lat ? lat->nchains : 0; }
 size_t sm_workspace_bytes(const sm_lattice* lat) { return lat ? Ws::bytes(lat) : 0; }
 

@@ -9,12 +9,15 @@
 // re-reads of neighbouring tiles are served by L2.  Coordinates wrap
 // periodically per element, so tiles larger than a small lattice, partial
 // edge tiles and ragged batches all work (the antiperiodic sign is in U).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <vector>
 
 #include "common.cuh"
 #include "internal.h"
+#include "tile.cuh"
 
 namespace sm {
 
@@ -106,129 +109,51 @@ __global__ void __launch_bounds__(kTX* kTY) k_ddagd_tile(const ChainInfo* __rest
   st_sp(out, off + x + (long long)L * t, diag * unpack(st[dy][dx]) - (R)0.5 * o);
 }
 
-// FP32 form for large lattices: 64 x 16 tiles (4 output sites per thread,
-// halo overhead 1.33x on `in` instead of 1.69x), staged with cp.async:
-// every thread issues all of its 16-byte global -> shared copies before one
-// wait, so a block has its whole 42 KB region in flight.  Interior tiles
-// (whose region needs no periodic wrap) skip the wrap arithmetic.
-constexpr int kBX = 64, kBY = 16, kBT = 512;
-constexpr int kBPX = kBX + 4, kBPY = kBY + 4;
-constexpr int kBUX = kBX + 3, kBUY = kBY + 3;
-constexpr int kBDX = kBX + 2, kBDY = kBY + 2;
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-
 __global__ void __launch_bounds__(kBT) k_ddagd_tile_big(const ChainInfo* __restrict__ chains,
                                                         const int4* __restrict__ tiles,
                                                         const float* __restrict__ U,
                                                         const float* __restrict__ in,
-                                                        float* __restrict__ out) {
-  extern __shared__ float4 sm4[];
-  float4* sp = sm4;                   // [kBPY][kBPX]
-  float4* su = sp + kBPX * kBPY;      // [kBUY][kBUX]
-  float4* st = su + kBUX * kBUY;      // [kBDY][kBDX]
+                                                        float* __restrict__ out,
+                                                        const __grid_constant__ CUtensorMap tin,
+                                                        const __grid_constant__ CUtensorMap tU,
+                                                        int tma, int* err) {
+  extern __shared__ __align__(128) float4 sm4[];
+  __shared__ __align__(8) unsigned long long bar;
   const int4 tile = tiles[blockIdx.x];
-  const ChainInfo ci = chains[tile.x];
-  const int x0 = tile.y, t0 = tile.z, L = ci.L, T = ci.T;
-  const long long off = ci.off;
-  const int tid = threadIdx.x;
-  const float4* in4 = reinterpret_cast<const float4*>(in) + off;
-  const float4* U4 = reinterpret_cast<const float4*>(U) + off;
-  const bool interior = x0 >= 2 && x0 + kBX + 2 <= L && t0 >= 2 && t0 + kBY + 2 <= T;
-  if (interior) {
-    const float4* pin = in4 + (x0 - 2) + (long long)L * (t0 - 2);
-    const float4* pU = U4 + (x0 - 2) + (long long)L * (t0 - 2);
-    for (int i = tid; i < kBPX * kBPY; i += kBT) {
-      const int ly = i / kBPX, lx = i - ly * kBPX;
-      cp_async16(sp + i, pin + lx + (long long)L * ly);
-    }
-    for (int i = tid; i < kBUX * kBUY; i += kBT) {
-      const int ly = i / kBUX, lx = i - ly * kBUX;
-      cp_async16(su + i, pU + lx + (long long)L * ly);
-    }
-  } else {
-    auto wx = [&](int x) { x %= L; return x < 0 ? x + L : x; };
-    auto wt = [&](int t) { t %= T; return t < 0 ? t + T : t; };
-    for (int i = tid; i < kBPX * kBPY; i += kBT) {
-      const int ly = i / kBPX, lx = i - ly * kBPX;
-      cp_async16(sp + i, in4 + wx(x0 - 2 + lx) + (long long)L * wt(t0 - 2 + ly));
-    }
-    for (int i = tid; i < kBUX * kBUY; i += kBT) {
-      const int ly = i / kBUX, lx = i - ly * kBUX;
-      cp_async16(su + i, U4 + wx(x0 - 2 + lx) + (long long)L * wt(t0 - 2 + ly));
-    }
-  }
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-  __syncthreads();
+  ddagd_big_tile(sm4, chains[tile.x], tile, U, in, out, nullptr, tma ? &tin : nullptr,
+                 tma ? &tU : nullptr, &bar, err);
+}
 
-  const float diag = (float)(2.0 + ci.m0);
-  auto S = [](float4 v) { return Sp<float>{{v.x, v.y}, {v.z, v.w}}; };
-  // the link of the x (t) direction of a site: one 8-byte half of its float4
-  const float2* su2 = reinterpret_cast<const float2*>(su);
-  auto UX = [&](int u) { const float2 v = su2[2 * u]; return Cx<float>{v.x, v.y}; };
-  auto UT = [&](int u) { const float2 v = su2[2 * u + 1]; return Cx<float>{v.x, v.y}; };
-  // t = D in on the (kBX + 2) x (kBY + 2) region.  Threads 0 .. 383 walk the
-  // 64 main columns in 6 strips of 3 rows (warps stay on one row: no bank
-  // conflicts; t-neighbours and U_t(n - t) come from registers); threads
-  // 384 .. 419 do the two halo columns site by site.
-  constexpr int kDRows = kBDY / 6;
-  auto dsite = [&](int dx, int dy, const Sp<float>& pm, const Sp<float>& pc,
-                   const Sp<float>& pn, Cx<float> utm) {
-    const int p = (dy + 1) * kBPX + dx + 1, u = (dy + 1) * kBUX + dx + 1;
-    const float4 uu = su[u];
-    const Sp<float> o = hop_sum<false, float>(S(sp[p + 1]), S(sp[p - 1]), pn, pm, {uu.x, uu.y},
-                                              UX(u - 1), {uu.z, uu.w}, utm);
-    const Sp<float> tv = diag * pc - 0.5f * o;
-    st[dy * kBDX + dx] = make_float4(tv.a.re, tv.a.im, tv.b.re, tv.b.im);
-    return Cx<float>{uu.z, uu.w};
+// Tensor maps of `in` and U for TMA staging (single-chain lattices large
+// enough for interior tiles).  Returns false where TMA is not used.
+bool make_tile_tmaps(const sm_lattice* L, const float* in, const float* U, CUtensorMap* tin,
+                     CUtensorMap* tU) {
+  if (L->nchains != 1) return false;
+  const ChainInfo& ci = L->chains[0];
+  if (ci.L < kBX + 4 || ci.T < kBY + 4) return false;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  if (!encode) return false;
+  const cuuint64_t dims[2] = {2 * (cuuint64_t)ci.L, (cuuint64_t)ci.T};
+  const cuuint64_t strides[1] = {16 * (cuuint64_t)ci.L};
+  const cuuint32_t ebox[2] = {1, 1};
+  const cuuint32_t bin[2] = {2 * kBPX, kBPY}, bU[2] = {2 * kBUX, kBUY};
+  auto enc = [&](CUtensorMap* m, const float* base, const cuuint32_t* box) {
+    return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<float*>(base), dims, strides,
+                  box, ebox, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
   };
-  if (tid < 6 * kBX) {
-    const int dx = tid % kBX + 1, dy0 = (tid / kBX) * kDRows;
-    int p = (dy0 + 1) * kBPX + dx + 1;
-    Sp<float> pm = S(sp[p - kBPX]), pc = S(sp[p]);
-    Cx<float> utm = UT((dy0 + 1) * kBUX + dx + 1 - kBUX);
-#pragma unroll
-    for (int j = 0; j < kDRows; ++j, p += kBPX) {
-      const Sp<float> pn = S(sp[p + kBPX]);
-      utm = dsite(dx, dy0 + j, pm, pc, pn, utm);
-      pm = pc;
-      pc = pn;
-    }
-  } else if (tid < 6 * kBX + 2 * kBDY) {
-    const int k = tid - 6 * kBX;
-    const int dx = k < kBDY ? 0 : kBDX - 1, dy = k % kBDY;
-    const int p = (dy + 1) * kBPX + dx + 1, u = (dy + 1) * kBUX + dx + 1;
-    dsite(dx, dy, S(sp[p - kBPX]), S(sp[p]), S(sp[p + kBPX]), UT(u - kBUX));
-  }
-  __syncthreads();
-
-  // D^dag down a 4-row column strip per thread (64 columns x 4 strips): the
-  // t-neighbours and U_t(n - t) of the strip come from registers
-  constexpr int kRows = kBY / (kBT / kBX);
-  const int tx = tid % kBX, ty0 = (tid / kBX) * kRows;
-  const int x = x0 + tx;
-  int d = (ty0 + 1) * kBDX + tx + 1, u = (ty0 + 2) * kBUX + tx + 2;
-  Sp<float> tm = S(st[d - kBDX]), tc = S(st[d]);
-  Cx<float> utm = UT(u - kBUX);
-#pragma unroll
-  for (int j = 0; j < kRows; ++j, d += kBDX, u += kBUX) {
-    const Sp<float> tn = S(st[d + kBDX]);
-    const float4 uu = su[u];
-    const int t = t0 + ty0 + j;
-    if (x < L && t < T) {
-      const Sp<float> o = hop_sum<true, float>(S(st[d + 1]), S(st[d - 1]), tn, tm, {uu.x, uu.y},
-                                               UX(u - 1), {uu.z, uu.w}, utm);
-      const Sp<float> r = diag * tc - 0.5f * o;
-      reinterpret_cast<float4*>(out)[off + x + (long long)L * t] =
-          make_float4(r.a.re, r.a.im, r.b.re, r.b.im);
-    }
-    tm = tc;
-    tc = tn;
-    utm = {uu.z, uu.w};
-  }
+  return enc(tin, in, bin) && enc(tU, U, bU);
 }
 
 static int make_tiles(sm_lattice* lat, int tx, int ty, int4** d, int* n) {
@@ -245,6 +170,17 @@ static int make_tiles(sm_lattice* lat, int tx, int ty, int4** d, int* n) {
   return SM_OK;
 }
 
+// Each chain's range in the 64 x 16 tile table (before the chain table is
+// uploaded).
+void big_tile_ranges(sm_lattice* lat) {
+  int first = 0;
+  for (ChainInfo& ci : lat->chains) {
+    ci.tb0 = first;
+    ci.ntb = ((ci.L + kBX - 1) / kBX) * ((ci.T + kBY - 1) / kBY);
+    first += ci.ntb;
+  }
+}
+
 // Tile table of a lattice: {chain, x0, t0, 0} per tile (at lattice creation).
 int build_tile_table(sm_lattice* lat) {
   const int rc = make_tiles(lat, kTX, kTY, &lat->d_tiles, &lat->ntiles);
@@ -256,12 +192,15 @@ template <typename R>
 int launch_ddagd(Ctx& c, const R* U, const R* in, R* out) {
   if (sizeof(R) == 4 && c.L->N >= (1 << 18)) {
     // large FP32 batches: big tiles (the small-tile table stays for small ones)
-    const size_t smem = sizeof(float4) * (kBPX * kBPY + kBUX * kBUY + kBDX * kBDY);
+    const size_t smem = kBigSmemBytes;
     cudaError_t e = cudaFuncSetAttribute(k_ddagd_tile_big,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail(SM_ERR_CUDA, "ddagd attribute: %s", cudaGetErrorString(e));
+    CUtensorMap tin, tU;
+    const bool tma = make_tile_tmaps(c.L, (const float*)in, (const float*)U, &tin, &tU);
     k_ddagd_tile_big<<<c.L->ntiles_big, kBT, smem, c.s>>>(
-        c.L->d_chains, c.L->d_tiles_big, (const float*)U, (const float*)in, (float*)out);
+        c.L->d_chains, c.L->d_tiles_big, (const float*)U, (const float*)in, (float*)out, tin, tU,
+        tma ? 1 : 0, c.L->d_err);
     return launched(c.st, "ddagd_tile_big");
   }
   k_ddagd_tile<R><<<c.L->ntiles, kTX * kTY, 0, c.s>>>(c.L->d_chains, c.L->d_tiles, U, in, out);

@@ -3,6 +3,7 @@
 // kernel launchers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -23,6 +24,17 @@ struct sm_lattice {
   int4* d_tiles_big;  // 64 x 16 tiles of its large-lattice FP32 form
   int ntiles_big;
   int cg_variant;     // chain-resident mixed CG kernel chosen by sm_autotune_cg (-1: default)
+  // mixed batches: chains of at most 4096 sites (solved chain-resident on the
+  // side stream) and the mask of the others (solved grid-wide)
+  int nsmall;
+  int* d_small_list;
+  int nbig;           // chains of the 4-block cluster shape (128 x 128), and their list
+  int* d_big_list;
+  unsigned char* d_grid_mask;
+  std::vector<unsigned char> grid_mask;
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
+  int* d_err;  // device-side error word (a bounded wait that gave up)
   int device;
   int* h_pinned;  // small pinned host buffer for per-call readbacks
   cudaEvent_t ev[2];  // readback events of the CG loop
@@ -34,6 +46,8 @@ namespace sm {
 int fail(int code, const char* fmt, ...);
 // Counts one kernel launch and checks the launch for errors.
 int launched(sm_stats* st, const char* what);
+// Adjusts the process-wide launch count (CUDA-graph capture and replay).
+void add_launches(long long n);
 
 // Per-chain CG scalars (device).
 struct CgChain {
@@ -68,6 +82,7 @@ struct Ws {
   CgChain* cgc;        // [nchains]
   double* out;         // [8][nchains]
   int* flags;          // [nchains] per-chain masks
+  int* acc;            // [2][nchains] accumulated CG flags and iterations (deferred mode)
   int* n_active;       // [1]
   int* h_n_active;     // not in ws: pinned host word (see Ctx)
 
@@ -88,6 +103,12 @@ struct Ctx {
   // into chain_flags and returns SM_OK.
   bool strict = true;
   std::vector<int> chain_flags;
+  // Deferred mode (trajectories whose solves are all chain-resident, and
+  // CUDA-graph capture): cg_solve does not read its results back; each
+  // chain's flags and iteration count are accumulated on the device in
+  // w.acc and read once at the end.
+  bool deferred = false;
+  bool capturing = false;  // inside a CUDA-graph capture (no profiling events)
 
   int init(const sm_lattice* lat, void* ws, size_t nbytes, void* stream, sm_stats* stats);
   dim3 grid() const { return dim3((unsigned)L->nblocks); }
@@ -121,15 +142,38 @@ int launch_copy_links_masked(Ctx& c, double* dst, const double* src, const int* 
 
 // Fused D^dag D (ddagd.cu).
 int build_tile_table(sm_lattice* lat);
+bool make_tile_tmaps(const sm_lattice* L, const float* in, const float* U, CUtensorMap* tin,
+                     CUtensorMap* tU);
+void big_tile_ranges(sm_lattice* lat);
 template <typename R>
 int launch_ddagd(Ctx& c, const R* U, const R* in, R* out);
 
 // Chain-resident CG (cg_chain.cu): one block per chain.
 bool chain_cg_fits(const sm_lattice* L, int prec);
 bool chain_variant_applies(const sm_lattice* L, int v);
-constexpr int kChainVariants = 4;
+bool big_chain_shape(const ChainInfo& ci);
+constexpr int kChainVariants = 5;
 int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
                     const sm_cg_params& cg);
+
+// Sets the launch attributes of the chain-resident kernel a solve with
+// these parameters will use (done before a CUDA-graph capture).
+int chain_cg_prepare(const sm_lattice* L, const sm_cg_params& cg);
+// True if every solve with these parameters takes the chain-resident path.
+bool chain_cg_selected(const sm_lattice* L, const sm_cg_params& cg);
+int chain_cg_accumulate(Ctx& c);
+int chain_cg_launch_list(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
+                         const sm_cg_params& cg);
+
+// The tiled grid-wide mixed iteration (cg_tiled.cu) for batches of 2^18
+// sites or more: n iterations of P, AP, XR on r, x, p (in place), Ap.
+bool tiled_cg_applies(const sm_lattice* L);
+int tiled_cg_iterate(Ctx& c, const float* U32, float* r, float* x, float* p, float* Ap,
+                     double tol2, double delta2, int maxit, int n);
+
+// Kernel times of deferred solves and their site-iterations (solver.cu);
+// call after the stream has been synchronised.
+int profile_collect_deferred(const sm_lattice* L, const int* chain_iters);
 
 // CG on D^dag D (solver.cu).  b, x FP64; x is overwritten.  If iters/relres
 // are non-NULL they receive host copies.  Synchronises.

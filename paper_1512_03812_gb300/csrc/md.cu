@@ -408,45 +408,55 @@ int sm_md_step(const sm_lattice* lat, double* q, double* p, const double* phi,
   return chain_failures(c, "sm_md_step");
 }
 
-int sm_hmc_trajectory(const sm_lattice* lat, double* q, const double* p0, const double* eta,
-                      const double* u, const sm_md_params* md, void* ws, size_t ws_bytes,
-                      double* dH, double* H0, int* accepted, double* p_out, double* q_md,
-                      sm_stats* stats, void* stream) {
-  Ctx c;
-  SM_TRY(c.init(lat, ws, ws_bytes, stream, stats));
-  SM_TRY(check_md(md));
-  if (md->n < 1 || !(md->tau > 0)) return fail(SM_ERR_ARG, "md: n >= 1 and tau > 0 required");
-  SM_TRY(fields_ok({q, p0, eta}, "sm_hmc_trajectory"));
-  if (!u || !dH || !accepted) return fail(SM_ERR_ARG, "sm_hmc_trajectory: NULL host output");
-  if ((p_out && !al16(p_out)) || (q_md && !al16(q_md)))
-    return fail(SM_ERR_ARG, "sm_hmc_trajectory: unaligned output");
-  const int nc = lat->nchains;
-  const size_t lbytes = sizeof(double) * 2 * (size_t)lat->N;
-  const sm_cg_params& cg = md->cg;
-  sm_cg_params cgH = cg;  // the S_F solves of H
-  if (md->tol_action > 0.0) cgH.tol = md->tol_action;
-  double* out = c.w.out;  // [8][nc]: K0, SG0, SF0, K1, SG1, SF1
-  c.strict = false;       // a failing chain is rejected, the others go on
+}  // extern "C"
 
-  // heatbath phi = D^dag eta at the starting links; H at the start
+namespace sm {
+
+// The device part of one HMC update of every chain (Sec. 2.1): heatbath
+// phi = D^dag eta, H at the start, the MD trajectory, H at the end.  Enqueues
+// only (no host synchronisation when c.deferred).  Energies land in
+// c.w.out = [K0, SG0, SF0, K1, SG1, SF1][nchains].
+static int hmc_enqueue(Ctx& c, double* q, const double* p0, const double* eta,
+                       const sm_md_params& md) {
+  const int nc = c.L->nchains;
+  const size_t lbytes = sizeof(double) * 2 * (size_t)c.L->N;
+  const sm_cg_params& cg = md.cg;
+  sm_cg_params cgH = cg;  // the S_F solves of H
+  if (md.tol_action > 0.0) cgH.tol = md.tol_action;
+  double* out = c.w.out;
+  if (c.deferred) SM_CU(cudaMemsetAsync(c.w.acc, 0, 2 * sizeof(int) * nc, c.s));
   SM_TRY(make_links(c, q, c.w.U64, c.w.U32, cg));
   SM_TRY(launch_dslash<double>(c, c.w.U64, eta, c.w.phi, true, nullptr, 0.0));
   SM_CU(cudaMemcpyAsync(c.w.qsave, q, lbytes, cudaMemcpyDeviceToDevice, c.s));
   SM_CU(cudaMemcpyAsync(c.w.pw, p0, lbytes, cudaMemcpyDeviceToDevice, c.s));
   SM_TRY(cg_solve(c, c.w.U64, c.w.U32, c.w.phi, c.w.xi, cgH, nullptr, nullptr));
   SM_TRY(launch_energies(c, q, c.w.pw, c.w.phi, c.w.xi, out, out + nc, out + 2 * nc));
-
-  // molecular dynamics
-  SM_TRY(md_run(c, q, c.w.pw, c.w.phi, *md, md->tau / md->n, md->n));
-
-  // H at the end
+  SM_TRY(md_run(c, q, c.w.pw, c.w.phi, md, md.tau / md.n, md.n));
   SM_TRY(make_links(c, q, c.w.U64, c.w.U32, cg));
   SM_TRY(cg_solve(c, c.w.U64, c.w.U32, c.w.phi, c.w.xi, cgH, nullptr, nullptr));
-  SM_TRY(launch_energies(c, q, c.w.pw, c.w.phi, c.w.xi, out + 3 * nc, out + 4 * nc, out + 5 * nc));
-  std::vector<double> h(6 * (size_t)nc);
-  SM_CU(cudaMemcpyAsync(h.data(), out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c.s));
-  SM_CU(cudaStreamSynchronize(c.s));
+  return launch_energies(c, q, c.w.pw, c.w.phi, c.w.xi, out + 3 * nc, out + 4 * nc, out + 5 * nc);
+}
 
+// Reads H (and, in deferred mode, the solves' flags), takes the Metropolis
+// decisions and restores the links of rejected chains.  Synchronises.
+static int hmc_finish(Ctx& c, double* q, const double* u, double* dH, double* H0, int* accepted,
+                      double* p_out, double* q_md) {
+  const int nc = c.L->nchains;
+  const size_t lbytes = sizeof(double) * 2 * (size_t)c.L->N;
+  std::vector<double> h(6 * (size_t)nc);
+  std::vector<int> acc(2 * (size_t)nc, 0);
+  SM_CU(cudaMemcpyAsync(h.data(), c.w.out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c.s));
+  if (c.deferred)
+    SM_CU(cudaMemcpyAsync(acc.data(), c.w.acc, sizeof(int) * acc.size(), cudaMemcpyDeviceToHost, c.s));
+  SM_CU(cudaStreamSynchronize(c.s));
+  if (c.deferred) {
+    c.chain_flags.assign(nc, 0);
+    for (int i = 0; i < nc; ++i) {
+      c.chain_flags[i] = acc[i];
+      c.st->chain_iterations += acc[nc + i];
+    }
+    SM_TRY(profile_collect_deferred(c.L, acc.data() + nc));
+  }
   // Metropolis: accept iff dH <= 0 or u < exp(-dH); non-finite dH rejects
   std::vector<int> reject(nc);
   bool any_nan = false, any_reject = false;
@@ -470,8 +480,110 @@ int sm_hmc_trajectory(const sm_lattice* lat, double* q, const double* p0, const 
     SM_TRY(launch_copy_links_masked(c, q, c.w.qsave, c.w.flags));
   }
   SM_TRY(c.sync());
-  if (any_nan) return fail(SM_ERR_NAN, "sm_hmc_trajectory: non-finite Delta H (chain rejected)");
-  return chain_failures(c, "sm_hmc_trajectory");
+  if (any_nan) return fail(SM_ERR_NAN, "hmc: non-finite Delta H (chain rejected)");
+  return chain_failures(c, "hmc");
+}
+
+static bool all_chain_resident(const sm_lattice* L, const sm_md_params& md) {
+  sm_cg_params cgH = md.cg;
+  if (md.tol_action > 0.0) cgH.tol = md.tol_action;
+  return chain_cg_selected(L, md.cg) && chain_cg_selected(L, cgH);
+}
+
+}  // namespace sm
+
+// A captured HMC trajectory (see sm_hmc_graph_create).
+struct sm_hmc_graph {
+  const sm_lattice* lat;
+  double* q;
+  void* ws;
+  size_t ws_bytes;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  long long kernels;  // kernel nodes: launches per replay
+};
+
+extern "C" {
+
+int sm_hmc_trajectory(const sm_lattice* lat, double* q, const double* p0, const double* eta,
+                      const double* u, const sm_md_params* md, void* ws, size_t ws_bytes,
+                      double* dH, double* H0, int* accepted, double* p_out, double* q_md,
+                      sm_stats* stats, void* stream) {
+  Ctx c;
+  SM_TRY(c.init(lat, ws, ws_bytes, stream, stats));
+  SM_TRY(check_md(md));
+  if (md->n < 1 || !(md->tau > 0)) return fail(SM_ERR_ARG, "md: n >= 1 and tau > 0 required");
+  SM_TRY(fields_ok({q, p0, eta}, "sm_hmc_trajectory"));
+  if (!u || !dH || !accepted) return fail(SM_ERR_ARG, "sm_hmc_trajectory: NULL host output");
+  if ((p_out && !al16(p_out)) || (q_md && !al16(q_md)))
+    return fail(SM_ERR_ARG, "sm_hmc_trajectory: unaligned output");
+  c.strict = false;  // a failing chain is rejected, the others go on
+  c.deferred = all_chain_resident(lat, *md);
+  SM_TRY(hmc_enqueue(c, q, p0, eta, *md));
+  return hmc_finish(c, q, u, dH, H0, accepted, p_out, q_md);
+}
+
+int sm_hmc_graph_create(const sm_lattice* lat, double* q, const double* p0, const double* eta,
+                        const sm_md_params* md, void* ws, size_t ws_bytes, sm_hmc_graph** out,
+                        void* stream) {
+  if (!out) return fail(SM_ERR_ARG, "sm_hmc_graph_create: out is NULL");
+  *out = nullptr;
+  if (!stream) return fail(SM_ERR_ARG, "sm_hmc_graph_create: needs a non-default stream");
+  Ctx c;
+  SM_TRY(c.init(lat, ws, ws_bytes, stream, nullptr));
+  SM_TRY(check_md(md));
+  if (md->n < 1 || !(md->tau > 0)) return fail(SM_ERR_ARG, "md: n >= 1 and tau > 0 required");
+  SM_TRY(fields_ok({q, p0, eta}, "sm_hmc_graph_create"));
+  if (!all_chain_resident(lat, *md))
+    return fail(SM_ERR_ARG, "sm_hmc_graph_create: every solve must be chain-resident "
+                            "(SM_CG_AUTO or SM_CG_CHAIN with chains that fit)");
+  SM_TRY(chain_cg_prepare(lat, md->cg));
+  SM_TRY(c.sync());
+  c.strict = false;
+  c.deferred = true;
+  c.capturing = true;
+  const long long before = sm_launch_count();
+  SM_CU(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
+  const int rc = hmc_enqueue(c, q, p0, eta, *md);
+  const long long captured = sm_launch_count() - before;
+  add_launches(-captured);  // captured launches run only when the graph is replayed
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c.s, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(SM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  cudaGraphExec_t x = nullptr;
+  const cudaError_t e2 = cudaGraphInstantiate(&x, g, 0);
+  if (e2 != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(SM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e2));
+  }
+  *out = new sm_hmc_graph{lat, q, ws, ws_bytes, g, x, captured};
+  return SM_OK;
+}
+
+int sm_hmc_graph_run(sm_hmc_graph* gr, const double* u, double* dH, double* H0, int* accepted,
+                     sm_stats* stats, void* stream) {
+  if (!gr) return fail(SM_ERR_ARG, "sm_hmc_graph_run: graph is NULL");
+  if (!u || !dH || !accepted) return fail(SM_ERR_ARG, "sm_hmc_graph_run: NULL host output");
+  Ctx c;
+  SM_TRY(c.init(gr->lat, gr->ws, gr->ws_bytes, stream, stats));
+  c.strict = false;
+  c.deferred = true;
+  SM_CU(cudaGraphLaunch(gr->exec, c.s));
+  add_launches(gr->kernels);
+  c.st->kernel_launches += gr->kernels;
+  return hmc_finish(c, gr->q, u, dH, H0, accepted, nullptr, nullptr);
+}
+
+int sm_hmc_graph_destroy(sm_hmc_graph* gr) {
+  if (!gr) return SM_OK;
+  if (gr->exec) cudaGraphExecDestroy(gr->exec);
+  if (gr->graph) cudaGraphDestroy(gr->graph);
+  delete gr;
+  return SM_OK;
 }
 
 }  // extern "C"

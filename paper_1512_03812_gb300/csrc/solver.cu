@@ -55,6 +55,7 @@ struct CgArgs {
   double tol2, delta2;
   int maxit;
   int mixed;
+  const unsigned char* grid_mask;  // if set, only chains with mask 1 take the grid path
 };
 
 #define CHAIN_PROLOGUE                     \
@@ -75,6 +76,7 @@ __device__ __forceinline__ Sp<double> to_d(Sp<double> v) { return v; }
 template <typename R>
 __global__ void __launch_bounds__(kBlock) k_cg_init(Geo g, CgArgs<R> a) {
   CHAIN_PROLOGUE
+  if (a.grid_mask && !a.grid_mask[c_]) return;  // solved by the chain-resident kernel
   const Site s = site_of(g, ci, c_);
   double v[1] = {0.0};
   if (s.valid) {
@@ -202,6 +204,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_b(Geo g, CgArgs<R> a) {
 __global__ void __launch_bounds__(kBlock) k_cg_res_d(Geo g, CgArgs<float> a, const double* xhi,
                                                      const float* x, int all) {
   CHAIN_PROLOGUE
+  if (a.grid_mask && !a.grid_mask[c_]) return;
   if (!all && !cc->need_update) return;
   const Site s = site_of(g, ci, c_);
   if (!s.valid) return;
@@ -224,6 +227,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_res_d(Geo g, CgArgs<float> a, con
 __global__ void __launch_bounds__(kBlock) k_cg_res_r(Geo g, CgArgs<float> a, double* xhi,
                                                      int all) {
   CHAIN_PROLOGUE
+  if (a.grid_mask && !a.grid_mask[c_]) return;
   if (!all && !cc->need_update) return;
   const Site s = site_of(g, ci, c_);
   double v[1] = {0.0};
@@ -275,10 +279,31 @@ struct Profile {
   bool on = false;
   bool ready = false;
   cudaEvent_t e0[2], e1[2], e2[2];  // chunk start, after iterations, after residual
+  // deferred solves: one event pair per solve, collected when the caller
+  // has synchronised (profile_collect_deferred)
+  static constexpr int kPool = 256;
+  cudaEvent_t d0[kPool], d1[kPool];
+  int nd = 0;
   double iter_ms = 0, res_ms = 0;
   long long batched = 0, site_iters = 0;
 };
 static Profile g_prof;
+
+// Adds the kernel times of the deferred solves recorded since the last call
+// (the stream has been synchronised) and the site-iterations of `iters`.
+int profile_collect_deferred(const sm_lattice* L, const int* chain_iters) {
+  if (!g_prof.on) return SM_OK;
+  for (int i = 0; i < g_prof.nd; ++i) {
+    float ms = 0.f;
+    SM_CU(cudaEventElapsedTime(&ms, g_prof.d0[i], g_prof.d1[i]));
+    g_prof.iter_ms += ms;
+  }
+  g_prof.nd = 0;
+  if (chain_iters)
+    for (int c = 0; c < L->nchains; ++c)
+      g_prof.site_iters += (long long)chain_iters[c] * L->chains[c].L * L->chains[c].T;
+  return SM_OK;
+}
 
 static int prof_record(cudaEvent_t* e, int slot, cudaStream_t s) {
   if (!g_prof.on) return SM_OK;
@@ -299,8 +324,20 @@ static int prof_collect(int slot, bool residual) {
   return SM_OK;
 }
 
+// Chains outside the grid path of a mixed batch start with no pending state.
+__global__ void k_cg_reset_masked(CgChain* cgc, const unsigned char* mask, int n) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n && !mask[c]) {
+    cgc[c].state = 0;
+    cgc[c].need_update = 0;
+  }
+}
+
 template <typename R>
 static int iterate(Ctx& c, CgArgs<R>& a, int n) {
+  if (a.mixed && tiled_cg_applies(c.L))  // large batches: the tiled iteration
+    return tiled_cg_iterate(c, (const float*)a.U, (float*)a.r, (float*)a.x, (float*)a.pa,
+                            (float*)a.t, a.tol2, a.delta2, a.maxit, n);
   for (int k = 0; k < n; ++k) {
     k_cg_a<R><<<c.grid(), kBlock, 0, c.s>>>(c.g, a);
     int rc = launched(c.st, "cg_a");
@@ -397,11 +434,23 @@ int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, doubl
   if (cg.algo == SM_CG_CHAIN && !fits)
     return fail(SM_ERR_ARG, "cg_solve: a chain is too large for the chain-resident solver");
   const bool chain = cg.algo == SM_CG_CHAIN || (cg.algo == SM_CG_AUTO && fits);
+  // A batch of both kinds (AUTO, mixed): the chains that fit are solved
+  // chain-resident on the side stream while the others iterate grid-wide.
+  const bool hybrid = !chain && cg.algo == SM_CG_AUTO && mixed && c.L->nsmall > 0 && !c.deferred;
 
   SM_CU(cudaMemsetAsync(c.w.n_active, 0, sizeof(int), c.s));
   long long batched = 0, updates = 0;
   int rc;
   const int chunk = 8;
+  if (chain && c.deferred) {
+    // no readback: the chain's flags and iterations accumulate on the device
+    const bool timed = g_prof.on && !c.capturing && g_prof.nd < Profile::kPool;
+    if (timed) SM_CU(cudaEventRecord(g_prof.d0[g_prof.nd], c.s));
+    if ((rc = chain_cg_launch(c, U64, U32, b, x, cg))) return rc;
+    if (timed) SM_CU(cudaEventRecord(g_prof.d1[g_prof.nd++], c.s));
+    c.st->cg_solves++;
+    return chain_cg_accumulate(c);
+  }
   if (chain) {
     if ((rc = prof_record(g_prof.e0, 0, c.s))) return rc;
     if ((rc = chain_cg_launch(c, U64, U32, b, x, cg))) return rc;
@@ -409,9 +458,25 @@ int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, doubl
     SM_CU(cudaStreamSynchronize(c.s));
     if ((rc = prof_collect(0, false))) return rc;
   } else if (mixed) {
+    if (hybrid) {
+      af.grid_mask = c.L->d_grid_mask;
+      k_cg_reset_masked<<<(c.L->nchains + 255) / 256, 256, 0, c.s>>>(c.w.cgc, af.grid_mask,
+                                                                     c.L->nchains);
+      if ((rc = launched(c.st, "cg_reset_masked"))) return rc;
+      SM_CU(cudaEventRecord(c.L->ev_fork, c.s));
+      SM_CU(cudaStreamWaitEvent(c.L->side, c.L->ev_fork, 0));
+      Ctx cs = c;
+      cs.s = c.L->side;
+      if ((rc = chain_cg_launch_list(cs, U64, U32, b, x, cg))) return rc;
+      SM_CU(cudaEventRecord(c.L->ev_join, c.L->side));
+    }
     k_cg_init<float><<<c.grid(), kBlock, 0, c.s>>>(c.g, af);
     if ((rc = launched(c.st, "cg_init"))) return rc;
     if ((rc = run<float>(c, af, af, chunk, cg.maxit, &batched, &updates))) return rc;
+    if (hybrid) {
+      SM_CU(cudaStreamWaitEvent(c.s, c.L->ev_join, 0));
+      SM_CU(cudaStreamSynchronize(c.s));
+    }
   } else {
     CgArgs<double> ad{};
     ad.U = U64;
@@ -448,6 +513,9 @@ int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, doubl
       updates += ch.need_update;
     }
     batched = mx;
+  } else if (hybrid) {
+    for (int i = 0; i < c.L->nchains; ++i)
+      if (!c.L->grid_mask[i]) updates += h[i].need_update;
   }
   c.st->cg_solves++;
   c.st->cg_iterations += batched;
@@ -535,6 +603,10 @@ extern "C" int sm_profile_enable(int on) {
       SM_CU(cudaEventCreate(&g_prof.e0[i]));
       SM_CU(cudaEventCreate(&g_prof.e1[i]));
       SM_CU(cudaEventCreate(&g_prof.e2[i]));
+    }
+    for (int i = 0; i < Profile::kPool; ++i) {
+      SM_CU(cudaEventCreate(&g_prof.d0[i]));
+      SM_CU(cudaEventCreate(&g_prof.d1[i]));
     }
     g_prof.ready = true;
   }

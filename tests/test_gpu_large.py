@@ -54,6 +54,28 @@ def test_2048_dslash_and_fused_ddagd_every_site(torch, big):
     assert rel_err(out32, ref) < 4e-6
 
 
+def test_512_single_chain_tma_paths(torch):
+    """A single 512 x 512 chain takes the TMA-staged tiles (interior) and the
+    cp.async ones (boundary) in both the fused D^dag D and the tiled CG."""
+    import paper_1512_03812_gb300 as P
+    L = T = 512
+    m0 = sw.kappa_to_m0(0.24)
+    lat = P.Lattice(L, T, 2.0, m0)
+    q = I.hot_links(L, T, 91)
+    psi = I.spinor(L, T, 92)
+    U64, U32 = lat.links(torch.tensor(q, device="cuda"))
+    pd = torch.tensor(psi, device="cuda")
+    out = lat.apply_DdagD(U32, pd.to(torch.complex64)).cpu().numpy().reshape(T, L, 2)
+    olat = sw.Lattice(L, T, 2.0, m0)
+    ref = sw.apply_DdagD(olat, sw.links(q.reshape(T, L, 2)), psi.reshape(T, L, 2))
+    assert rel_err(out, ref) < 4e-6
+    x, iters, relres = lat.cg_solve(U64, U32, pd, P.CG(tol=1e-10, prec="mixed", delta=0.01))
+    assert relres[0] <= 1e-10
+    r = pd - lat.apply_DdagD(U64, x)
+    assert float(torch.linalg.vector_norm(r)) <= 1.0000001e-10 * float(torch.linalg.vector_norm(pd))
+    assert lat.check() == 0
+
+
 def test_2048_mixed_cg_true_residual(torch, big):
     P, lat, olat, q, psi, U64, U32 = big
     b = torch.tensor(psi, device="cuda")
@@ -62,6 +84,7 @@ def test_2048_mixed_cg_true_residual(torch, big):
     assert relres[0] <= 1e-10
     r = b - lat.apply_DdagD(U64, x)
     assert float(torch.linalg.vector_norm(r)) <= 1.0000001e-10 * float(torch.linalg.vector_norm(b))
+    assert lat.check() == 0
 
 
 def test_256_ragged_chains_sampled(torch):

@@ -152,7 +152,7 @@ def test_cg_layouts_agree(torch):
         assert rel_err(b.chain(xg, c), b.chain(xc, c)) < 1e-12
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_chain_cg_kernel_variants_64x64(torch, variant):
     """Every kernel variant of the chain-resident mixed CG (strided, column
     512x8, column 256x16, two-block cluster) on 64x64 chains: the FP64 true
@@ -180,6 +180,34 @@ def test_chain_cg_kernel_variants_64x64(torch, variant):
                            "adapted_nested_fg", 0.25, 1, M=2, solver=sw.Solver(1e-13))
     assert abs(dH[0] - ro.dH) < 1e-6, (dH[0], ro.dH)
     assert bool(acc[0]) == ro.accepted
+
+
+def test_mixed_batch_with_128x128_chains(torch):
+    """A batch of small chains and 128 x 128 chains is solved chain-resident
+    throughout: the small ones one block each, the large ones by 4-block
+    clusters (rows exchanged through distributed shared memory)."""
+    import paper_1512_03812_gb300 as P
+    dims = [(128, 128), (64, 64), (16, 16), (128, 128), (48, 48)]
+    b = batch(torch, dims=dims, betas=(2.0, 1.0, 4.0, 2.0, 1.5), kappas=(0.24, 0.22, 0.2, 0.25, 0.23))
+    q, phi = b.q(), b.spinor()
+    U64, U32 = b.lat.links(b.dev(q))
+    x64, _, _ = b.lat.cg_solve(U64, U32, b.dev(phi), cg(1e-12))
+    xm, iters, relres = b.lat.cg_solve(U64, U32, b.dev(phi),
+                                       P.CG(tol=1e-10, prec="mixed", delta=0.01, algo="chain"))
+    assert (relres <= 1e-10).all(), relres
+    r = b.dev(phi) - b.lat.apply_DdagD(U64, xm)
+    for c in range(len(dims)):
+        assert np.linalg.norm(b.chain(r, c)) <= 1.0000001e-10 * np.linalg.norm(b.chain(phi, c))
+        assert rel_err(b.chain(xm, c), b.chain(x64, c)) < 1e-8
+    # one short trajectory of the whole batch; chain 0 (128 x 128) against the oracle
+    p, eta = b.p(), b.eta()
+    md = P.MD(scheme="adapted_nested_fg", tau=0.2, n=1, M=2,
+              cg=P.CG(tol=1e-12, prec="mixed", delta=0.01))
+    dH, H0, acc = b.lat.hmc_trajectory(b.dev(q), b.dev(p), b.dev(eta), 0.5, md)
+    ro = ig.hmc_trajectory(b.olat[0], b.chain(q, 0), b.chain(p, 0), b.chain(eta, 0), 0.5,
+                           "adapted_nested_fg", 0.2, 1, M=2, solver=sw.Solver(1e-13))
+    assert abs(dH[0] - ro.dH) < 1e-6, (dH[0], ro.dH)
+    assert b.lat.check() == 0
 
 
 def test_chain_solver_rejects_oversized_chains(torch):
