@@ -54,10 +54,10 @@ NUM_SMS = 152
 # DRAM traffic of one launch of the chain-resident kernel from the ncu
 # capture in profiles/cg_chain_mixed_64x64x200.md; reported only while the
 # kernel source is unchanged since the capture.
-NCU_TRAFFIC = {"kernel": "k_cg_chain_mixed<8,512>",
-               "sources": {"paper_1512_03812_gb300/csrc/cg_chain.cu": "1571bd342ed6a2b9",
-                           "paper_1512_03812_gb300/csrc/common.cuh": "df919ebc12c4bab8"},
-               "dram_bytes_per_launch": 276316416 + 333173504}
+NCU_TRAFFIC = {"kernel": "k_cg_chain_cluster<8,256,2>",
+               "sources": {"paper_1512_03812_gb300/csrc/cg_chain.cu": "d3922942409cc196",
+                           "paper_1512_03812_gb300/csrc/common.cuh": "078132e7c68d198a"},
+               "dram_bytes_per_launch": 84524800 + 36106496}
 
 
 def _sha16(path):
@@ -66,9 +66,17 @@ def _sha16(path):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def ncu_traffic():
-    ok = all(_sha16(p) == h for p, h in NCU_TRAFFIC["sources"].items())
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or
+    None if that capture is of another kernel or its sources have changed."""
+    ok = kernel == NCU_TRAFFIC["kernel"] and all(
+        _sha16(p) == h for p, h in NCU_TRAFFIC["sources"].items())
     return NCU_TRAFFIC["dram_bytes_per_launch"] if ok else None
+
+
+# the chain-resident CG kernels by variant index (sm_set_cg_variant)
+CHAIN_KERNELS = ["k_cg_chain_mixed<8,512>", "k_cg_chain_col<8,512>", "k_cg_chain_col<16,256>",
+                 "k_cg_chain_cluster<8,256,2>", "k_cg_chain_cluster<4,512,2>"]
 
 
 def kappa_to_m0(k):
@@ -376,13 +384,14 @@ def run_ours(args):
         f_mhz = (clk or {}).get("sm_mhz") or 2070.0
         peak = NUM_SMS * SMEM_BYTES_PER_CLK_PER_SM * f_mhz * 1e6 / 1e9
         ach = SMEM_BYTES_PER_SITE_ITER * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
-        roofline = {"bound": "smem", "kernel": "k_cg_chain_mixed (chain-resident CG)",
+        kname = CHAIN_KERNELS[tune["variant"]] if tune else CHAIN_KERNELS[0]
+        roofline = {"bound": "smem", "kernel": kname + " (chain-resident CG)",
                     "achieved": round(ach, 1), "peak": round(peak, 1), "unit": "GB/s",
                     "frac": round(ach / peak, 4),
                     "peak_source": f"{NUM_SMS} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x "
                                    f"{f_mhz:.0f} MHz (median SM clock under load)",
                     "bytes_per_site_iter": SMEM_BYTES_PER_SITE_ITER,
-                    "traffic": ncu_traffic(), "traffic_unit": "DRAM bytes per launch (ncu)",
+                    "traffic": ncu_traffic(kname), "traffic_unit": "DRAM bytes per launch (ncu)",
                     "hbm_equivalent": {"achieved": round(hbm_eq, 1), "peak": hbm,
                                        "unit": "GB/s", "frac": round(hbm_eq / hbm, 4),
                                        "bytes_per_site_iter": bps, "peak_source": src}}
@@ -529,7 +538,11 @@ def run_other(args):
                        cg_delta=args.delta, l2="flushed between steps (256 MiB write)"),
         "acceptance": round(float(np.mean(np.concatenate(accs))), 4),
         "last_step_stats": st, "gpu_launches": int(binding.launch_count() - n0),
-        "roofline": {"bound": "hbm", "kernel": "cg iteration (grid-wide k_cg_a + k_cg_b)",
+        "roofline": {"bound": "hbm",
+                     "kernel": ("chain-resident CG (one block per small chain, 4-block clusters "
+                                "for 128x128 chains; data on chip: HBM-equivalent bytes)"
+                                if args.workload == "batched" else
+                                "tiled grid-wide CG iteration (k_cgt_p + k_cgt_ap + k_cgt_xr)"),
                      "achieved": round(ach, 1), "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                      "frac": round(ach / float(peaks["hbm_gbs"]), 4), "peak_source": src,
                      "bytes_per_site_iter": bps, "site_iters": prof["site_iters"],
