@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "stream.cuh"
 #include "tile.cuh"
 
 namespace sm {
@@ -22,6 +23,8 @@ namespace sm {
 struct TiledArgs {
   Geo g;
   const int4* tiles;
+  const int4* strips;  // streaming form (stream.cuh), if the lattice allows it
+  int TT;
   const float* U;
   float* r;
   float* x;
@@ -104,6 +107,66 @@ __global__ void __launch_bounds__(kBT) k_cgt_ap(TiledArgs a,
   }
 }
 
+// The same on the streaming form: one strip per warp, block partials in the
+// chain's range of the strip table.
+__global__ void __launch_bounds__(kSThreads, 4) k_cgt_ap_stream(TiledArgs a) {
+  __shared__ __align__(16) float4 ring[kSWarps * kSRing];
+  __shared__ double red[kSWarps];
+  __shared__ bool last;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int4 s = a.strips[blockIdx.x * kSWarps + w];
+  const int c = s.x;  // the same for every warp of the block
+  CgChain* cc = a.cgc + c;
+  if (cc->state != 1) return;
+  const ChainInfo ci = a.g.chains[c];
+  double v = ddagd_stream_strip<true>(ring + w * kSRing, a.g.chains, s, a.TT, a.U, a.p, a.Ap);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double part = 0.0;
+#pragma unroll
+    for (int k = 0; k < kSWarps; ++k) part += red[k];
+    __stcg(a.partials + blockIdx.x, part);
+    __threadfence();
+    last = atomicAdd(a.counters + c, 1u) == (unsigned)ci.nsb - 1u;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // |D p|^2 of the chain: its blocks' partials in block order
+  double tot = 0.0;
+  for (int i = threadIdx.x; i < ci.nsb; i += kSThreads) tot += __ldcg(a.partials + ci.sb0 + i);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+  __syncthreads();
+  if (lane == 0) red[w] = tot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tot = 0.0;
+#pragma unroll
+    for (int k = 0; k < kSWarps; ++k) tot += red[k];
+    a.counters[c] = 0u;
+    if (tot > 0.0 && isfinite(tot)) {
+      cc->alpha = cc->rr / tot;
+    } else {
+      cc->alpha = 0.0;
+      cc->flags |= 2;
+      cc->state = 0;
+      atomicSub(a.n_active, 1);
+    }
+  }
+}
+
+int cgt_stream_occupancy() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cgt_ap_stream, kSThreads, 0) !=
+      cudaSuccess)
+    return 0;
+  return n;
+}
+
 __global__ void __launch_bounds__(kBlock) k_cgt_xr(TiledArgs a) {
   const int c = a.g.blk_chain[blockIdx.x];
   CgChain* cc = a.cgc + c;
@@ -146,6 +209,8 @@ int tiled_cg_iterate(Ctx& c, const float* U32, float* r, float* x, float* p, flo
   TiledArgs a{};
   a.g = c.g;
   a.tiles = c.L->d_tiles_big;
+  a.strips = c.L->d_stream;
+  a.TT = c.L->stream_tt;
   a.U = U32;
   a.r = r;
   a.x = x;
@@ -159,16 +224,24 @@ int tiled_cg_iterate(Ctx& c, const float* U32, float* r, float* x, float* p, flo
   a.tol2 = tol2;
   a.delta2 = delta2;
   a.maxit = maxit;
-  const cudaError_t e = cudaFuncSetAttribute(k_cgt_ap, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kBigSmemBytes);
-  if (e != cudaSuccess) return fail(SM_ERR_CUDA, "tiled CG attribute: %s", cudaGetErrorString(e));
+  const bool stream = c.L->stream_ok;
   CUtensorMap tin, tU;
-  const int tma = make_tile_tmaps(c.L, p, U32, &tin, &tU) ? 1 : 0;
+  int tma = 0;
+  if (!stream) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        k_cgt_ap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBigSmemBytes);
+    if (e != cudaSuccess)
+      return fail(SM_ERR_CUDA, "tiled CG attribute: %s", cudaGetErrorString(e));
+    tma = make_tile_tmaps(c.L, p, U32, &tin, &tU) ? 1 : 0;
+  }
   for (int k = 0; k < n; ++k) {
     k_cgt_p<<<c.grid(), kBlock, 0, c.s>>>(a);
     int rc = launched(c.st, "cgt_p");
     if (rc) return rc;
-    k_cgt_ap<<<c.L->ntiles_big, kBT, kBigSmemBytes, c.s>>>(a, tin, tU, tma);
+    if (stream)
+      k_cgt_ap_stream<<<c.L->nstream, kSThreads, 0, c.s>>>(a);
+    else
+      k_cgt_ap<<<c.L->ntiles_big, kBT, kBigSmemBytes, c.s>>>(a, tin, tU, tma);
     if ((rc = launched(c.st, "cgt_ap"))) return rc;
     k_cgt_xr<<<c.grid(), kBlock, 0, c.s>>>(a);
     if ((rc = launched(c.st, "cgt_xr"))) return rc;

@@ -545,6 +545,10 @@ int sm_lattice_create(int nchains, const int* L, const int* T, const double* bet
   big_tile_ranges(lat);
   lat->cg_variant = -1;
   cudaGetDevice(&lat->device);
+  if (const int rc = stream_ranges(lat)) {
+    delete lat;
+    return rc;
+  }
   cudaError_t e = cudaMalloc(&lat->d_chains, sizeof(ChainInfo) * nchains);
   if (e == cudaSuccess) e = cudaMalloc(&lat->d_blk_chain, sizeof(int) * blk);
   if (e == cudaSuccess) e = cudaMalloc(&lat->d_chain_list, sizeof(int) * nchains);
@@ -620,6 +624,7 @@ int sm_lattice_destroy(sm_lattice* lat) {
   if (lat->ev_fork) cudaEventDestroy(lat->ev_fork);
   if (lat->ev_join) cudaEventDestroy(lat->ev_join);
   if (lat->d_tiles_big) cudaFree(lat->d_tiles_big);
+  if (lat->d_stream) cudaFree(lat->d_stream);
   if (lat->h_pinned) cudaFreeHost(lat->h_pinned);
   if (lat->ev[0]) cudaEventDestroy(lat->ev[0]);
   if (lat->ev[1]) cudaEventDestroy(lat->ev[1]);

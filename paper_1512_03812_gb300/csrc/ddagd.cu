@@ -13,10 +13,12 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
 #include "internal.h"
+#include "stream.cuh"
 #include "tile.cuh"
 
 namespace sm {
@@ -124,6 +126,95 @@ __global__ void __launch_bounds__(kBT) k_ddagd_tile_big(const ChainInfo* __restr
                  tma ? &tU : nullptr, &bar, err);
 }
 
+// Streaming form: one strip per warp (stream.cuh).
+__global__ void __launch_bounds__(kSThreads, 4) k_ddagd_stream(const ChainInfo* __restrict__ chains,
+                                                             const int4* __restrict__ strips,
+                                                             int TT, const float* __restrict__ U,
+                                                             const float* __restrict__ in,
+                                                             float* __restrict__ out) {
+  __shared__ __align__(16) float4 ring[kSWarps * kSRing];
+  const int w = threadIdx.x >> 5;
+  ddagd_stream_strip<false>(ring + w * kSRing, chains, strips[blockIdx.x * kSWarps + w], TT, U,
+                            in, out);
+}
+
+int ddagd_stream_occupancy() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ddagd_stream, kSThreads, 0) !=
+      cudaSuccess)
+    return 0;
+  return n;
+}
+
+// Strips per chain for strip height TT, and the blocks they fill.
+static long long stream_blocks(const sm_lattice* lat, int TT) {
+  long long nb = 0;
+  for (const ChainInfo& ci : lat->chains) {
+    const long long strips =
+        (long long)((ci.L + kSOut - 1) / kSOut) * ((ci.T + TT - 1) / TT);
+    nb += (strips + kSWarps - 1) / kSWarps;
+  }
+  return nb;
+}
+
+int stream_ranges(sm_lattice* lat) {
+  // every chain must be wide enough that the 64-column windows waste little
+  // (at most 30 % more columns than the lattice has)
+  lat->stream_ok = lat->N >= (1 << 18);
+  for (const ChainInfo& ci : lat->chains)
+    if (10LL * kSW * ((ci.L + kSOut - 1) / kSOut) > 13LL * ci.L) lat->stream_ok = false;
+  if (!lat->stream_ok) return SM_OK;
+  // the lowest strip height whose blocks all fit on the GPU at once (one
+  // wave); launches with fewer strips per SM than that lose bandwidth
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(SM_ERR_CUDA, "device attribute");
+  const int occ = std::min(ddagd_stream_occupancy(), cgt_stream_occupancy());
+  if (occ <= 0) return fail(SM_ERR_CUDA, "streaming D^dag D: no occupancy");
+  const long long slots = (long long)nsm * occ;
+  int tmax = 0;
+  for (const ChainInfo& ci : lat->chains) tmax = std::max(tmax, ci.T);
+  int lo = 8, hi = std::max(8, tmax);
+  if (stream_blocks(lat, hi) > slots) {
+    lo = hi = 32;  // more than one wave whatever the height
+  }
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if (stream_blocks(lat, mid) <= slots) hi = mid; else lo = mid + 1;
+  }
+  lat->stream_tt = lo;
+  int first = 0;
+  for (ChainInfo& ci : lat->chains) {
+    const long long strips =
+        (long long)((ci.L + kSOut - 1) / kSOut) * ((ci.T + lo - 1) / lo);
+    ci.sb0 = first;
+    ci.nsb = (int)((strips + kSWarps - 1) / kSWarps);
+    first += ci.nsb;
+  }
+  lat->nstream = first;
+  return SM_OK;
+}
+
+static int build_stream_table(sm_lattice* lat) {
+  if (!lat->stream_ok) return SM_OK;
+  std::vector<int4> t;
+  t.reserve((size_t)lat->nstream * kSWarps);
+  for (int c = 0; c < lat->nchains; ++c) {
+    const ChainInfo& ci = lat->chains[c];
+    const size_t first = t.size();
+    // vertically adjacent strips walk in opposite directions
+    for (int y = 0, k = 0; y < ci.T; y += lat->stream_tt, ++k)
+      for (int x = 0; x < ci.L; x += kSOut) t.push_back(make_int4(c, x, y, 1 + (k & 1)));
+    while ((t.size() - first) % kSWarps) t.push_back(make_int4(c, 0, 0, 0));
+  }
+  cudaError_t e = cudaMalloc(&lat->d_stream, sizeof(int4) * t.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(lat->d_stream, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(SM_ERR_CUDA, "strip table: %s", cudaGetErrorString(e));
+  return SM_OK;
+}
+
 // Tensor maps of `in` and U for TMA staging (single-chain lattices large
 // enough for interior tiles).  Returns false where TMA is not used.
 bool make_tile_tmaps(const sm_lattice* L, const float* in, const float* U, CUtensorMap* tin,
@@ -183,15 +274,23 @@ void big_tile_ranges(sm_lattice* lat) {
 
 // Tile table of a lattice: {chain, x0, t0, 0} per tile (at lattice creation).
 int build_tile_table(sm_lattice* lat) {
-  const int rc = make_tiles(lat, kTX, kTY, &lat->d_tiles, &lat->ntiles);
+  int rc = make_tiles(lat, kTX, kTY, &lat->d_tiles, &lat->ntiles);
   if (rc) return rc;
-  return make_tiles(lat, kBX, kBY, &lat->d_tiles_big, &lat->ntiles_big);
+  if ((rc = make_tiles(lat, kBX, kBY, &lat->d_tiles_big, &lat->ntiles_big))) return rc;
+  return build_stream_table(lat);
 }
 
 template <typename R>
 int launch_ddagd(Ctx& c, const R* U, const R* in, R* out) {
+  if (sizeof(R) == 4 && c.L->stream_ok) {
+    k_ddagd_stream<<<c.L->nstream, kSThreads, 0, c.s>>>(c.L->d_chains, c.L->d_stream,
+                                                         c.L->stream_tt, (const float*)U,
+                                                         (const float*)in, (float*)out);
+    return launched(c.st, "ddagd_stream");
+  }
   if (sizeof(R) == 4 && c.L->N >= (1 << 18)) {
-    // large FP32 batches: big tiles (the small-tile table stays for small ones)
+    // large FP32 batches of narrow chains: big tiles (the small-tile table
+    // stays for small batches)
     const size_t smem = kBigSmemBytes;
     cudaError_t e = cudaFuncSetAttribute(k_ddagd_tile_big,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -23,6 +23,13 @@ struct sm_lattice {
   int ntiles;
   int4* d_tiles_big;  // 64 x 16 tiles of its large-lattice FP32 form
   int ntiles_big;
+  // streaming FP32 D^dag D (stream.cuh): kSWarps strips {chain, xs, ts, 1}
+  // per block ({chain, 0, 0, 0} pads a chain's last block), strips of
+  // stream_tt rows; stream_ok if every chain is wide enough for it
+  bool stream_ok;
+  int stream_tt;
+  int nstream;  // blocks
+  int4* d_stream;
   int cg_variant;     // chain-resident mixed CG kernel chosen by sm_autotune_cg (-1: default)
   // mixed batches: chains of at most 4096 sites (solved chain-resident on the
   // side stream) and the mask of the others (solved grid-wide)
@@ -145,6 +152,11 @@ int build_tile_table(sm_lattice* lat);
 bool make_tile_tmaps(const sm_lattice* L, const float* in, const float* U, CUtensorMap* tin,
                      CUtensorMap* tU);
 void big_tile_ranges(sm_lattice* lat);
+// Chooses the strip height and each chain's block range of the streaming
+// form (before the chain table is uploaded).
+int stream_ranges(sm_lattice* lat);
+int ddagd_stream_occupancy();
+int cgt_stream_occupancy();
 template <typename R>
 int launch_ddagd(Ctx& c, const R* U, const R* in, R* out);
 

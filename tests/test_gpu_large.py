@@ -54,11 +54,14 @@ def test_2048_dslash_and_fused_ddagd_every_site(torch, big):
     assert rel_err(out32, ref) < 4e-6
 
 
-def test_512_single_chain_tma_paths(torch):
-    """A single 512 x 512 chain takes the TMA-staged tiles (interior) and the
-    cp.async ones (boundary) in both the fused D^dag D and the tiled CG."""
+@pytest.mark.parametrize("L,T", [(512, 512), (130, 2048)])
+def test_single_chain_large_fp32_paths(torch, L, T):
+    """2^18 sites or more in one chain: 512 x 512 takes the warp-streaming
+    D^dag D (60-column strips) in both sm_apply_DdagD and the tiled CG;
+    130 x 2048 is too narrow for 64-column windows (3 strips would read 192
+    columns) and takes the 64 x 16 tiles instead, TMA-staged in the interior
+    (x0 = 64) and cp.async-staged at the boundary."""
     import paper_1512_03812_gb300 as P
-    L = T = 512
     m0 = sw.kappa_to_m0(0.24)
     lat = P.Lattice(L, T, 2.0, m0)
     q = I.hot_links(L, T, 91)
@@ -107,3 +110,28 @@ def test_256_ragged_chains_sampled(torch):
         assert rel_err(b.chain(out, c), ref) < 4e-6
         r = b.chain(psi, c) - sw.apply_DdagD(ol, U, b.chain(x, c))
         assert np.linalg.norm(r) <= 1.0000001e-10 * np.linalg.norm(b.chain(psi, c))
+
+
+def test_stream_ragged_batch_every_site(torch):
+    """A ragged batch on the streaming form: a strip of 1 column at the right
+    edge (301 = 5 x 60 + 1), one of 16 (256), whole strips (240), and a chain
+    of 37 rows, fewer than a strip's window, whose rows wrap inside it."""
+    import paper_1512_03812_gb300 as P
+    shapes = [(301, 500), (256, 700), (240, 37)]
+    betas, kappas = [2.0, 4.0, 1.0], [0.24, 0.25, 0.22]
+    b = Batch(shapes, betas, kappas, seed=95)
+    assert b.lat.N >= 1 << 18
+    q, psi = b.q(), b.spinor()
+    U64, U32 = b.lat.links(b.dev(q))
+    out = b.lat.apply_DdagD(U32, b.dev(psi, torch.complex64))
+    x, iters, relres = b.lat.cg_solve(U64, U32, b.dev(psi), P.CG(tol=1e-10, prec="mixed",
+                                                                  delta=0.01))
+    assert (relres <= 1e-10).all()
+    for c in range(len(shapes)):
+        ol = b.olat[c]
+        U = sw.links(b.chain(q, c))
+        ref = sw.apply_DdagD(ol, U, b.chain(psi, c))
+        assert rel_err(b.chain(out, c), ref) < 4e-6
+        r = b.chain(psi, c) - sw.apply_DdagD(ol, U, b.chain(x, c))
+        assert np.linalg.norm(r) <= 1.0000001e-10 * np.linalg.norm(b.chain(psi, c))
+    assert b.lat.check() == 0
