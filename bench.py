@@ -54,10 +54,20 @@ NUM_SMS = 152
 # DRAM traffic of one launch of the chain-resident kernel from the ncu
 # capture in profiles/cg_chain_mixed_64x64x200.md; reported only while the
 # kernel source is unchanged since the capture.
-NCU_TRAFFIC = {"kernel": "k_cg_chain_cluster<8,256,2>",
-               "sources": {"paper_1512_03812_gb300/csrc/cg_chain.cu": "d3922942409cc196",
-                           "paper_1512_03812_gb300/csrc/common.cuh": "078132e7c68d198a"},
-               "dram_bytes_per_launch": 84524800 + 36106496}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# the committed ncu captures, keyed by kernel, with the sources they were
+# taken on: a changed source makes the figure stale (reported as null)
+NCU_CAPTURES = {
+    "k_cg_chain_cluster<8,256,2>": {
+        "sources": {"paper_1512_03812_gb300/csrc/cg_chain.cu": "d3922942409cc196",
+                    "paper_1512_03812_gb300/csrc/common.cuh": "078132e7c68d198a"},
+        "dram_bytes_per_launch": 84524800 + 36106496},
+    "k_ddagd_stream": {
+        "sources": {"paper_1512_03812_gb300/csrc/stream.cuh": "8cfb0bc8bcfed0e2",
+                    "paper_1512_03812_gb300/csrc/ddagd.cu": "0cc3a39f4068c6ef",
+                    "paper_1512_03812_gb300/csrc/common.cuh": "1d7d22c0e0d74bdf"},
+        "dram_bytes_per_launch": 134648064 + 28383488},
+}
 
 
 def _sha16(path):
@@ -68,10 +78,11 @@ def _sha16(path):
 
 def ncu_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, or
-    None if that capture is of another kernel or its sources have changed."""
-    ok = kernel == NCU_TRAFFIC["kernel"] and all(
-        _sha16(p) == h for p, h in NCU_TRAFFIC["sources"].items())
-    return NCU_TRAFFIC["dram_bytes_per_launch"] if ok else None
+    None if there is none or its sources have changed."""
+    cap = NCU_CAPTURES.get(kernel)
+    if cap is None or any(_sha16(p) != h for p, h in cap["sources"].items()):
+        return None
+    return cap["dram_bytes_per_launch"]
 
 
 # the chain-resident CG kernels by variant index (sm_set_cg_variant)
@@ -366,10 +377,30 @@ def run_ours(args):
             dev_max = max(dev_max, float(np.abs(d64[ok] - dm[ok]).max()) if ok.any() else 0.0)
             acc64.append(a64)
             qm.copy_(q64)
+        same = float(np.mean(np.concatenate(acc64) == np.concatenate(accm)))
         fp64 = {"traj_per_s": world * B * args.fp64_steps / (t64 / 1e3),
                 "acc": float(np.mean(np.concatenate(acc64))),
                 "acc_mixed_same_inputs": float(np.mean(np.concatenate(accm))),
-                "max_abs_dH_mixed_minus_fp64": dev_max, "steps": args.fp64_steps}
+                "same_decisions": same,
+                "max_abs_dH_mixed_minus_fp64": dev_max, "steps": args.fp64_steps,
+                "cg_tol": W["cg_tol"]}
+        if args.tight_tol > 0:
+            # the same comparison with both paths solving to a tighter true
+            # residual: the deviation follows the tolerance, not FP32 arithmetic
+            def md_at(prec):
+                return P.MD(scheme=W["scheme"], tau=W["tau"], n=W["n"], M=W["M"], fg=W["fg"],
+                            cg=P.CG(tol=args.tight_tol, maxit=50000, prec=prec, algo=args.algo,
+                                    delta=args.delta),
+                            tol_action=min(args.tight_tol, W["cg_tol_action"]))
+            qa, qb = q_start.clone(), q_start.clone()
+            da, _, aa = lat.hmc_trajectory(qa, pk[0], ek[0], uk[0], md_at("f64"), check=False)
+            db, _, ab = lat.hmc_trajectory(qb, pk[0], ek[0], uk[0], md_at("mixed"), check=False)
+            ok = np.isfinite(da) & np.isfinite(db)
+            fp64["tight_tol"] = {"cg_tol": args.tight_tol,
+                                 "max_abs_dH_mixed_minus_fp64":
+                                     float(np.abs(da[ok] - db[ok]).max()) if ok.any() else None,
+                                 "same_decisions": float(np.mean(aa == ab)), "trajectories": B}
+            del qa, qb
 
     # roofline of the dominant kernel: the CG solve.  The chain-resident form
     # (every chain of this workload fits) keeps U, p, t in shared memory and
@@ -380,16 +411,21 @@ def run_ours(args):
     ksec = prof["iter_ms"] / 1e3
     hbm_eq = bps * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
     chain = args.algo == "chain" or (args.algo == "auto" and args.prec == "mixed")
+    rates = binding.measure_peaks()
     if chain and args.prec == "mixed":
         f_mhz = (clk or {}).get("sm_mhz") or 2070.0
-        peak = NUM_SMS * SMEM_BYTES_PER_CLK_PER_SM * f_mhz * 1e6 / 1e9
+        nominal = NUM_SMS * SMEM_BYTES_PER_CLK_PER_SM * f_mhz * 1e6 / 1e9
+        peak = rates["smem_read_gbs"]
         ach = SMEM_BYTES_PER_SITE_ITER * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
         kname = CHAIN_KERNELS[tune["variant"]] if tune else CHAIN_KERNELS[0]
         roofline = {"bound": "smem", "kernel": kname + " (chain-resident CG)",
                     "achieved": round(ach, 1), "peak": round(peak, 1), "unit": "GB/s",
                     "frac": round(ach / peak, 4),
-                    "peak_source": f"{NUM_SMS} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x "
-                                   f"{f_mhz:.0f} MHz (median SM clock under load)",
+                    "peak_source": "measured in this run (sm_peak_smem_read: 16-byte shared "
+                                   "loads on every SM)",
+                    "peak_nominal": round(nominal, 1),
+                    "peak_nominal_source": f"{NUM_SMS} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x "
+                                           f"{f_mhz:.0f} MHz (median SM clock under load)",
                     "bytes_per_site_iter": SMEM_BYTES_PER_SITE_ITER,
                     "traffic": ncu_traffic(kname), "traffic_unit": "DRAM bytes per launch (ncu)",
                     "hbm_equivalent": {"achieved": round(hbm_eq, 1), "peak": hbm,
@@ -406,7 +442,7 @@ def run_ours(args):
     ddagd = None
     if not args.no_ddagd:
         ddagd = {"f32": measure_ddagd(torch, P, dev, prec="f32"),
-                 "f64": measure_ddagd(torch, P, dev, prec="f64")}
+                 "f64": measure_ddagd(torch, P, dev, prec="f64", rates=rates)}
     if rank != 0:
         return
     cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu) else None
@@ -426,6 +462,7 @@ def run_ours(args):
         "roofline": roofline,
         "fp64": fp64,
         "ddagd_2048": ddagd,
+        "measured_rates": rates,
         "clocks": clk,
         "cpu_baseline": cpu,
     }
@@ -526,9 +563,37 @@ def run_other(args):
     binding.profile_enable(False)
     st = lat.stats.as_dict()
     peaks, src = measured_peaks()
+    rates = binding.measure_peaks()
     ksec = prof["iter_ms"] / 1e3
     bps = CG_BYTES_PER_SITE_ITER["mixed"]
+    hbm = float(peaks["hbm_gbs"])
     ach = bps * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
+    common = {"site_iters": prof["site_iters"], "kernel_ms": round(prof["iter_ms"], 2),
+              "res_ms": round(prof["res_ms"], 2),
+              "kernel_share_of_step": round(prof["iter_ms"] / ms, 4), "traffic": None}
+    if args.workload == "batched":
+        # every chain is chain-resident: the iteration data stays in shared
+        # memory, so the bound is shared-memory bandwidth (HBM-equivalent
+        # bytes beside it for context)
+        sach = SMEM_BYTES_PER_SITE_ITER * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
+        roofline = dict({"bound": "smem",
+                         "kernel": "chain-resident CG (one block per small chain, 4-block "
+                                   "clusters for 128x128 chains)",
+                         "achieved": round(sach, 1), "peak": round(rates["smem_read_gbs"], 1),
+                         "unit": "GB/s", "frac": round(sach / rates["smem_read_gbs"], 4),
+                         "peak_source": "measured in this run (sm_peak_smem_read)",
+                         "bytes_per_site_iter": SMEM_BYTES_PER_SITE_ITER,
+                         "hbm_equivalent": {"achieved": round(ach, 1), "peak": hbm,
+                                            "frac": round(ach / hbm, 4),
+                                            "bytes_per_site_iter": bps, "peak_source": src}},
+                        **common)
+    else:
+        roofline = dict({"bound": "hbm",
+                         "kernel": "tiled grid-wide CG iteration (k_cgt_p + k_cgt_ap_stream + "
+                                   "k_cgt_xr)",
+                         "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(ach / hbm, 4), "peak_source": src,
+                         "bytes_per_site_iter": bps}, **common)
     print(json.dumps({
         "metric": "HMC trajectories/s", "value": round(B * args.steps / (ms / 1e3), 4),
         "unit": "trajectories/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -538,22 +603,16 @@ def run_other(args):
                        cg_delta=args.delta, l2="flushed between steps (256 MiB write)"),
         "acceptance": round(float(np.mean(np.concatenate(accs))), 4),
         "last_step_stats": st, "gpu_launches": int(binding.launch_count() - n0),
-        "roofline": {"bound": "hbm",
-                     "kernel": ("chain-resident CG (one block per small chain, 4-block clusters "
-                                "for 128x128 chains; data on chip: HBM-equivalent bytes)"
-                                if args.workload == "batched" else
-                                "tiled grid-wide CG iteration (k_cgt_p + k_cgt_ap + k_cgt_xr)"),
-                     "achieved": round(ach, 1), "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                     "frac": round(ach / float(peaks["hbm_gbs"]), 4), "peak_source": src,
-                     "bytes_per_site_iter": bps, "site_iters": prof["site_iters"],
-                     "kernel_ms": round(prof["iter_ms"], 2), "res_ms": round(prof["res_ms"], 2),
-                     "kernel_share_of_step": round(prof["iter_ms"] / ms, 4), "traffic": None},
+        "roofline": roofline, "measured_rates": rates,
         "clocks": clk}), flush=True)
 
 
 # ------------------------------------------------- D^dag D at 2048 x 2048 --
 
-def measure_ddagd(torch, P, dev, reps=20, prec="f32", warmup=3):
+DDAGD_FLOPS_PER_SITE = 112  # two stages of 4 hops x 11 flops + 12 for the diagonal
+
+
+def measure_ddagd(torch, P, dev, reps=20, prec="f32", warmup=3, rates=None):
     """Fused D^dag D (sm_apply_DdagD) on one 2048 x 2048 lattice: CUDA-event
     time per launch with L2 flushed before each launch; algorithmic bytes
     48 (FP32) or 96 (FP64) per site: read in and U once, write out once."""
@@ -594,7 +653,22 @@ def measure_ddagd(torch, P, dev, reps=20, prec="f32", warmup=3):
             "ms_median": round(ms, 4), "bytes_per_site": bps, "achieved": round(gbs, 1),
             "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
             "frac": round(gbs / float(peaks["hbm_gbs"]), 4), "peak_source": src,
-            "l2": "flushed before each launch (write 256 MiB, then read 256 MiB)", "reps": reps}
+            "l2": "flushed before each launch (write 256 MiB, then read 256 MiB)", "reps": reps,
+            "traffic": ncu_traffic("k_ddagd_stream") if prec == "f32" else None,
+            **fp64_roofline(ms, L * T, prec, rates)}
+
+
+def fp64_roofline(ms, sites, prec, rates):
+    """The FP64 stencil against the measured FP64 FMA rate (its bound on
+    GB300: 112 flops per 96 bytes needs ~7.8 TFLOP/s to keep up with HBM)."""
+    if prec != "f64" or not rates:
+        return {}
+    tf = DDAGD_FLOPS_PER_SITE * sites / (ms / 1e3) / 1e12
+    return {"alu": {"bound": "fp64", "flops_per_site": DDAGD_FLOPS_PER_SITE,
+                    "achieved_tflops": round(tf, 4),
+                    "peak_tflops": round(rates["fp64_tflops"], 4),
+                    "frac": round(tf / rates["fp64_tflops"], 4),
+                    "peak_source": "measured in this run (sm_peak_fma, FP64)"}}
 
 
 # ------------------------------------------------------- oracle (CPU) ------
@@ -651,8 +725,11 @@ def run_stencil(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     P.build()
+    from paper_1512_03812_gb300 import binding
+    rates = binding.measure_peaks()
     f32 = measure_ddagd(torch, P, dev, reps=args.steps, prec="f32", warmup=args.warmup)
-    f64 = measure_ddagd(torch, P, dev, reps=args.steps, prec="f64", warmup=args.warmup)
+    f64 = measure_ddagd(torch, P, dev, reps=args.steps, prec="f64", warmup=args.warmup,
+                        rates=rates)
     print(json.dumps({"metric": "fused D^dag D stencil, algorithmic GB/s", "value": f32["achieved"],
                       "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": f32["ms_median"], "higher_is_better": True,
@@ -662,8 +739,10 @@ def run_stencil(args):
                                        "256 MiB)"},
                       "roofline": {"bound": "hbm", "achieved": f32["achieved"],
                                    "peak": f32["peak"], "unit": "GB/s", "frac": f32["frac"],
-                                   "kernel": f32["kernel"], "traffic": None},
-                      "f64": f64}), flush=True)
+                                   "kernel": f32["kernel"],
+                                   "traffic": ncu_traffic(f32["kernel"]),
+                                   "traffic_unit": "DRAM bytes per launch (ncu)"},
+                      "f64": f64, "measured_rates": rates}), flush=True)
 
 
 def main():
@@ -676,6 +755,8 @@ def main():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "f64"])
     ap.add_argument("--therm", type=int, default=20)
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--tight-tol", type=float, default=1e-12,
+                    help="also compare Delta H of both paths at this CG tolerance (0: skip)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ddagd", action="store_true")
     ap.add_argument("--cg-variant", type=int, default=-1)

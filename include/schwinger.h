@@ -367,6 +367,24 @@ int sm_hmc_graph_run(sm_hmc_graph* g, const double* u, double* dH, double* H0, i
                      sm_stats* stats, void* stream);
 int sm_hmc_graph_destroy(sm_hmc_graph* g);
 
+/* ------------------------------------------------- measured GPU rates ---- */
+
+/* Micro-benchmarks of the rates the library's kernels are measured against
+ * (no counterpart in the paper: they calibrate rooflines on the device in
+ * use).  Each allocates and frees its own device memory, runs on the current
+ * device's default stream, synchronises, and returns SM_OK or SM_ERR_CUDA.
+ *
+ * sm_peak_fma: dense fused multiply-add throughput in TFLOP/s (2 flops per
+ *   FMA) of the FP64 (prec = SM_F64) or FP32 (SM_F32) pipes, from independent
+ *   FMA chains in every thread of a grid filling all SMs.
+ * sm_peak_l2_read: read bandwidth in GB/s of a `bytes`-sized buffer (at most
+ *   the L2 size for an L2 figure) read `passes` times after one warm pass.
+ * sm_peak_smem_read: shared-memory read bandwidth in GB/s over all SMs
+ *   (16-byte loads by every thread of resident blocks). */
+int sm_peak_fma(int prec, double* tflops);
+int sm_peak_l2_read(long long bytes, int passes, double* gbs);
+int sm_peak_smem_read(double* gbs);
+
 #ifdef __cplusplus
 }
 #endif

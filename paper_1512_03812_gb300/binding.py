@@ -80,6 +80,9 @@ _SIGS = {
     "sm_launch_count": (ctypes.c_longlong, []),
     "sm_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "sm_profile_read": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
+    "sm_peak_fma": (ctypes.c_int, [ctypes.c_int, _P]),
+    "sm_peak_l2_read": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, _P]),
+    "sm_peak_smem_read": (ctypes.c_int, [_P]),
     "sm_lattice_create": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     "sm_lattice_destroy": (ctypes.c_int, [_P]),
     "sm_lattice_sites": (ctypes.c_longlong, [_P]),
@@ -440,6 +443,19 @@ def profile_read(reset: bool = False) -> dict:
                                   ctypes.byref(s), 1 if reset else 0))
     return {"iter_ms": a.value, "res_ms": b.value, "batched_iters": n.value,
             "site_iters": s.value}
+
+
+def measure_peaks(l2_bytes: int = 48 << 20, l2_passes: int = 20) -> dict:
+    """Measured device rates (sm_peak_*): FP64 and FP32 FMA TFLOP/s, L2 read
+    GB/s over an `l2_bytes` buffer, shared-memory read GB/s."""
+    lib = load()
+    f64, f32, l2, smem = (ctypes.c_double() for _ in range(4))
+    _check(lib.sm_peak_fma(SM_F64, ctypes.byref(f64)))
+    _check(lib.sm_peak_fma(SM_F32, ctypes.byref(f32)))
+    _check(lib.sm_peak_l2_read(l2_bytes, l2_passes, ctypes.byref(l2)))
+    _check(lib.sm_peak_smem_read(ctypes.byref(smem)))
+    return {"fp64_tflops": f64.value, "fp32_tflops": f32.value, "l2_read_gbs": l2.value,
+            "l2_bytes": l2_bytes, "smem_read_gbs": smem.value}
 
 
 def launch_count() -> int:
