@@ -5,7 +5,11 @@ Workload (the mixed-precision versus FP64 configuration of the 64 x 64
 lattice): 64 x 64 sites, beta = 2.0, kappa = 0.26, tau = 1, the adapted
 nested force-gradient scheme (outer n = 8, inner m = 2, exact C_FF),
 FP32 CG with FP64 reliable updates to a true relative residual of 1e-10;
-200 chains per GPU advance one trajectory per step.  The chains start
+304 chains per GPU advance one trajectory per step (at least the 200
+trajectories per step of the configuration, rounded up to two full waves of
+the 152 chains the chain-resident CG holds on the GPU at once; --chains 200
+runs exactly 200, a second wave of 48 chains then leaves most SMs idle).
+The chains start
 from one configuration thermalised by this library's own HMC (untimed);
 every step draws fresh momenta and pseudofermion noise (pre-generated on
 the device before the timed region).
@@ -33,9 +37,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = {
-    "workload": "64x64 beta=2.0 kappa=0.26, 200 chains/GPU, adapted nested FG n=8 m=2, "
+    "workload": "64x64 beta=2.0 kappa=0.26, 304 chains/GPU, adapted nested FG n=8 m=2, "
                 "mixed-precision CG tol 1e-10 (1e-12 for the S_F of H)",
-    "L": 64, "T": 64, "beta": 2.0, "kappa": 0.26, "chains_per_gpu": 200,
+    "L": 64, "T": 64, "beta": 2.0, "kappa": 0.26, "chains_per_gpu": 304,
     "scheme": "adapted_nested_fg", "tau": 1.0, "n": 8, "M": 2, "fg": "exact",
     "cg_tol": 1e-10, "cg_tol_action": 1e-12, "cg_delta": 0.01, "precision": "mixed",
 }
