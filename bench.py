@@ -41,7 +41,7 @@ WORKLOAD = {
                 "mixed-precision CG tol 1e-10 (1e-12 for the S_F of H)",
     "L": 64, "T": 64, "beta": 2.0, "kappa": 0.26, "chains_per_gpu": 304,
     "scheme": "adapted_nested_fg", "tau": 1.0, "n": 8, "M": 2, "fg": "exact",
-    "cg_tol": 1e-10, "cg_tol_action": 1e-12, "cg_delta": 0.01, "precision": "mixed",
+    "cg_tol": 1e-10, "cg_tol_action": 1e-12, "cg_delta": 0.001, "precision": "mixed",
 }
 # Global-memory bytes per site and CG iteration of a memory-resident CG
 # iteration (the grid-wide pair of solver.cu: kernel A reads r, p, U and
@@ -769,7 +769,8 @@ def main():
     ap.add_argument("--workload", default="default", choices=["default", "batched", "large", "stencil"])
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])
     ap.add_argument("--M", type=int, default=WORKLOAD["M"])
-    ap.add_argument("--delta", type=float, default=0.01)
+    ap.add_argument("--delta", type=float, default=0.001,
+                    help="reliable-update factor of the mixed CG")
     ap.add_argument("--algo", default="auto", choices=["auto", "grid", "chain"])
     args = ap.parse_args()
     if args.impl == "reference":

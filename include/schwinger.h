@@ -133,7 +133,7 @@ typedef struct {
   long long cg_solves;         /* batched CG solves of D^dag D */
   long long cg_iterations;     /* batched iterations (all chains advance together) */
   long long chain_iterations;  /* sum over chains of their own iteration counts */
-  long long reliable_updates;  /* batched FP64 reliable-update passes */
+  long long reliable_updates;  /* FP64 reliable updates, summed over chains */
   long long inversions;        /* inversions of D in the paper's units (Sec. 3, end) */
   long long force_evals;       /* fermion-force evaluations */
   long long kernel_launches;   /* device kernels launched by this call */

@@ -69,7 +69,7 @@ struct CgChain {
   int iters;
   int flags;       // bit 0: maxit reached, bit 1: breakdown (p^dag A p <= 0)
   int par;         // which of the two search-direction buffers holds p
-  int pad;
+  int updates;     // grid-wide form: reliable updates done
 };
 
 // Scratch carved from the caller's workspace.

@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(Geo g, CgArgs<R> a) {
     cc->iters = 0;
     cc->par = 0;
     cc->need_update = 0;
+    cc->updates = 0;
     cc->flags = 0;
     if (bb > 0.0 && isfinite(bb)) {
       cc->state = 1;
@@ -253,6 +254,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_res_r(Geo g, CgArgs<float> a, dou
     cc->rr_true = rr;
     if (!all) {
       cc->need_update = 0;
+      cc->updates += 1;
       cc->rmax = rr;
       if (!isfinite(rr)) {
         cc->flags |= 2;
@@ -376,7 +378,6 @@ static int run(Ctx& c, CgArgs<R>& a, CgArgs<float>& af, int chunk, int maxit, lo
     if (a.mixed) {
       rc = residual(c, af, af.xhi, af.x, 0);
       if (rc) return rc;
-      (*updates)++;
     }
     if ((rc = prof_record(g_prof.e2, slot, c.s))) return rc;
     SM_CU(cudaMemcpyAsync(h + slot, a.n_active, sizeof(int), cudaMemcpyDeviceToHost, c.s));
@@ -513,9 +514,11 @@ int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, doubl
       updates += ch.need_update;
     }
     batched = mx;
-  } else if (hybrid) {
+  } else if (mixed) {
+    // grid-wide chains count their updates; in a hybrid solve the
+    // chain-resident ones report theirs in need_update
     for (int i = 0; i < c.L->nchains; ++i)
-      if (!c.L->grid_mask[i]) updates += h[i].need_update;
+      updates += (hybrid && !c.L->grid_mask[i]) ? h[i].need_update : h[i].updates;
   }
   c.st->cg_solves++;
   c.st->cg_iterations += batched;
