@@ -611,6 +611,138 @@ def run_other(args):
         "clocks": clk}), flush=True)
 
 
+# ------------------------------------- the paper's own numerical experiment --
+
+# Sec. 5 of the paper: a 32 x 32 lattice, beta = 1.0, m0 = -0.231367, one
+# thermalised configuration, 200 sets of momenta per integrator and step
+# size, trajectories of length tau = 2, micro step h / 10 for the nested
+# schemes (M = 5 inner leapfrog steps per half macro step).  Table 1 lists the
+# step size of each integrator at 90 % acceptance and its inversions of D.
+PAPER = {
+    "L": 32, "T": 32, "beta": 1.0, "m0": -0.231367, "tau": 2.0, "sets": 200, "M": 5,
+    # integrator, force-gradient form, Table 1 step size, its D^-1 per step
+    # and per trajectory as printed
+    "table1": [("five_stage", "exact", 0.0294, 6, 420),
+               ("nested_five_stage", "exact", 0.0286, 6, 408),
+               ("five_stage_fg", "exact", 0.0550, 10, 370),
+               ("five_stage_fg", "shifted", 0.0540, 8, 290),
+               ("nested_fg", "exact", 0.0560, 8, 285),
+               ("adapted_nested_fg", "exact", 0.0560, 8, 285)],
+    # |Delta H| against h (Fig. 1) for every integrator
+    "scan_h": (0.0125, 0.025, 0.05, 0.1),
+    "scan": [("leapfrog", "exact"), ("nested_leapfrog", "exact"), ("five_stage", "exact"),
+             ("nested_five_stage", "exact"), ("five_stage_fg", "exact"),
+             ("five_stage_fg", "shifted"), ("nested_fg", "exact"), ("adapted_nested_fg", "exact")],
+}
+
+
+def run_paper(args):
+    """The paper's experiment on this library: Table 1 (acceptance, |Delta H|
+    and inversions of D per trajectory at the printed step sizes) and the
+    |Delta H| against h scan of Fig. 1, 200 momentum sets each, as one batch
+    of 200 chains started from the same thermalised configuration."""
+    import torch
+
+    import paper_1512_03812_gb300 as P
+    Wp = PAPER
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    P.build()
+    L, T, B = Wp["L"], Wp["T"], Wp["sets"]
+    g = torch.Generator(device=dev)
+    g.manual_seed(1512)
+    cg = P.CG(tol=1e-10, maxit=50000, prec="mixed", delta=args.delta)
+
+    def draw(n, N):
+        p = torch.randn((N, 2), generator=g, device=dev, dtype=torch.float64)
+        e = torch.view_as_complex(torch.randn((N, 2, 2), generator=g, device=dev,
+                                              dtype=torch.float64) * math.sqrt(0.5)).contiguous()
+        u = torch.rand(n, generator=g, device=dev, dtype=torch.float64).cpu().numpy()
+        return p, e, u
+
+    # thermalisation: 8 chains from the ordered start, 50 trajectories
+    # accepted unconditionally, then Metropolis; chain 0 is the configuration
+    # (the paper's thermalised configuration is not available)
+    t0 = time.time()
+    nth = 8
+    th = P.Lattice([L] * nth, [T] * nth, Wp["beta"], Wp["m0"], device=dev)
+    q = torch.zeros((nth * L * T, 2), dtype=torch.float64, device=dev)
+    mdt = P.MD(scheme="adapted_nested_fg", tau=Wp["tau"], n=40, M=Wp["M"], cg=cg)
+    acc_th = []
+    for k in range(args.therm_paper):
+        p, e, u = draw(nth, nth * L * T)
+        _, _, a = th.hmc_trajectory(q, p, e, u if k >= 50 else np.zeros(nth), mdt, check=False)
+        if k >= 50:
+            acc_th.append(a)
+    q0 = q[:L * T].clone()
+    del th, q
+    log(f"paper: thermalised in {time.time() - t0:.1f}s")
+
+    lat = P.Lattice([L] * B, [T] * B, Wp["beta"], Wp["m0"], device=dev)
+    qb = q0.repeat(B, 1)
+
+    def measure(scheme, fg, h, merge=True):
+        n = int(math.ceil(Wp["tau"] / h - 1e-9))
+        md = P.MD(scheme=scheme, tau=Wp["tau"], n=n, M=Wp["M"], fg=fg, cg=cg, tol_action=1e-12,
+                  merge_kicks=merge)
+        p, e, u = draw(B, B * L * T)
+        q = qb.clone()
+        dH, _, acc = lat.hmc_trajectory(q, p, e, u, md, check=False)
+        st = lat.stats.as_dict()  # this call's counters
+        # a trajectory whose |Delta H| exceeds 10 has left the integrator's
+        # stability region (it is rejected with probability > 0.99995); its
+        # |Delta H| (up to 1e15 here) would swamp the mean of the others
+        ok = np.isfinite(dH)
+        a = np.abs(dH[ok])
+        stable = a[a <= 10.0]
+        return {"scheme": scheme, "fg": fg, "h": round(Wp["tau"] / n, 6), "n": n,
+                "M": Wp["M"] if "nested" in scheme else None,
+                "acceptance": round(float(np.mean(acc)), 4),
+                "acceptance_expected": round(float(np.mean(np.minimum(1.0, np.exp(-dH[ok])))), 4),
+                "median_abs_dH": float(np.median(a)),
+                "mean_abs_dH_stable": float(stable.mean()) if len(stable) else None,
+                "err_abs_dH_stable":
+                    float(stable.std() / math.sqrt(len(stable))) if len(stable) else None,
+                "unstable": int((a > 10.0).sum() + (~ok).sum()),
+                "mean_abs_dH_all": float(a.mean()),
+                "inversions_per_traj_md": int(st["inversions"])}
+
+    t1 = time.time()
+    table = []
+    for scheme, fg, h, per_step, per_traj in Wp["table1"]:
+        # the paper counts every kick of every step; adjacent kicks of the
+        # same force merged into one (same flow) need fewer inversions
+        r = measure(scheme, fg, h, merge=False)
+        r["inversions_per_traj_md_merged_kicks"] = measure(scheme, fg, h)["inversions_per_traj_md"]
+        r.update({"paper_h": h, "paper_inversions_per_step": per_step,
+                  "paper_inversions_per_traj": per_traj})
+        table.append(r)
+        log(f"paper table1 {scheme}/{fg} h={r['h']}: acc {r['acceptance']} median |dH| "
+            f"{r['median_abs_dH']:.4g} unstable {r['unstable']} inversions "
+            f"{r['inversions_per_traj_md']}")
+    scan = []
+    for scheme, fg in Wp["scan"]:
+        for h in Wp["scan_h"]:
+            scan.append(measure(scheme, fg, h))
+    dt = time.time() - t1
+    ntraj = B * (len(table) + len(scan))
+    print(json.dumps({
+        "metric": "paper workload: trajectories/s over the Table 1 and Fig. 1 runs",
+        "value": round(ntraj / dt, 3), "unit": "trajectories/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic (own thermalised start)",
+        "config": {"workload": "32x32 beta=1.0 m0=-0.231367 tau=2, 200 momentum sets per "
+                               "integrator and step size, nested micro step h/10 (M=5), mixed "
+                               "CG tol 1e-10 (1e-12 for the S_F of H)",
+                   "thermalisation": {"chains": nth, "trajectories": args.therm_paper,
+                                      "acceptance_after_50":
+                                          round(float(np.mean(np.concatenate(acc_th))), 4)
+                                          if acc_th else None}},
+        "inversions_counting": "D^-1 per trajectory in the MD (one D^dag D solve = 2; the "
+                               "two solves of H are not counted); Table 1 rows with every kick "
+                               "evaluated (as the paper counts), plus the merged-kick count",
+        "table1": table, "scan": scan}), flush=True)
+
+
 # ------------------------------------------------- D^dag D at 2048 x 2048 --
 
 DDAGD_FLOPS_PER_SITE = 112  # two stages of 4 hops x 11 flops + 12 for the diagonal
@@ -766,7 +898,9 @@ def main():
     ap.add_argument("--cg-variant", type=int, default=-1)
     ap.add_argument("--graph", action="store_true",
                     help="replay one captured trajectory (CUDA graph) per step")
-    ap.add_argument("--workload", default="default", choices=["default", "batched", "large", "stencil"])
+    ap.add_argument("--workload", default="default", choices=["default", "batched", "large", "stencil", "paper"])
+    ap.add_argument("--therm-paper", type=int, default=150,
+                    help="thermalisation trajectories of the paper workload")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])
     ap.add_argument("--M", type=int, default=WORKLOAD["M"])
     ap.add_argument("--delta", type=float, default=0.001,
@@ -777,6 +911,8 @@ def main():
         run_reference(args)
     elif args.workload == "stencil":
         run_stencil(args)
+    elif args.workload == "paper":
+        run_paper(args)
     elif args.workload != "default":
         run_other(args)
     else:
