@@ -49,9 +49,15 @@ WORKLOAD = {
 # FP32, 32 B in FP64).
 CG_BYTES_PER_SITE_ITER = {"mixed": (3 + 2) * 16 + (5 + 2) * 16, "f64": (3 + 2) * 32 + (5 + 2) * 32}
 # Shared-memory bytes per site and iteration of the chain-resident FP32 CG
-# (cg_chain.cu): p update 2 x 16, t = D p reads 5 p + 3 U and writes t
-# (9 x 16), D^dag t reads 5 t + 3 U + p (9 x 16).
-SMEM_BYTES_PER_SITE_ITER = 20 * 16
+# (cg_chain.cu), by kernel variant.  Strided layout (0): p update 2 x 16,
+# t = D p reads 5 p + 3 U and writes t (9 x 16), D^dag t reads 5 t + 3 U + p
+# (9 x 16).  Column layouts (1 to 4, and the 4-block cluster of 128 x 128
+# chains): the t-neighbours, their link U_t(n - t) and the site's own value
+# come from registers, so D p reads p at x +- 1, p at t + 1, U and U(n - x)
+# and writes t (6 x 16), D^dag t the same on t plus p (6 x 16).
+SMEM_BYTES_STRIDED = 20 * 16
+SMEM_BYTES_COLUMN = 14 * 16
+SMEM_BYTES_BY_VARIANT = [SMEM_BYTES_STRIDED] + [SMEM_BYTES_COLUMN] * 4
 # Shared-memory bandwidth per SM and clock (32 banks x 4 B).
 SMEM_BYTES_PER_CLK_PER_SM = 128
 NUM_SMS = 152
@@ -424,8 +430,10 @@ def run_ours(args):
         f_mhz = (clk or {}).get("sm_mhz") or 2070.0
         nominal = NUM_SMS * SMEM_BYTES_PER_CLK_PER_SM * f_mhz * 1e6 / 1e9
         peak = rates["smem_read_gbs"]
-        ach = SMEM_BYTES_PER_SITE_ITER * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
-        kname = CHAIN_KERNELS[tune["variant"]] if tune else CHAIN_KERNELS[0]
+        var = tune["variant"] if tune else 0
+        sbytes = SMEM_BYTES_BY_VARIANT[var]
+        ach = sbytes * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
+        kname = CHAIN_KERNELS[var]
         roofline = {"bound": "smem", "kernel": kname + " (chain-resident CG)",
                     "achieved": round(ach, 1), "peak": round(peak, 1), "unit": "GB/s",
                     "frac": round(ach / peak, 4),
@@ -434,7 +442,7 @@ def run_ours(args):
                     "peak_nominal": round(nominal, 1),
                     "peak_nominal_source": f"{NUM_SMS} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x "
                                            f"{f_mhz:.0f} MHz (median SM clock under load)",
-                    "bytes_per_site_iter": SMEM_BYTES_PER_SITE_ITER,
+                    "bytes_per_site_iter": sbytes,
                     "traffic": ncu_traffic(kname), "traffic_unit": "DRAM bytes per launch (ncu)",
                     "hbm_equivalent": {"achieved": round(hbm_eq, 1), "peak": hbm,
                                        "unit": "GB/s", "frac": round(hbm_eq / hbm, 4),
@@ -583,14 +591,17 @@ def run_other(args):
         # every chain is chain-resident: the iteration data stays in shared
         # memory, so the bound is shared-memory bandwidth (HBM-equivalent
         # bytes beside it for context)
-        sach = SMEM_BYTES_PER_SITE_ITER * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
+        # small chains take the strided kernel (320 B), the 128 x 128 ones the
+        # 4-block cluster in the column layout (224 B): the lower figure is
+        # used for all, so `achieved` is a lower bound
+        sach = SMEM_BYTES_COLUMN * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
         roofline = dict({"bound": "smem",
                          "kernel": "chain-resident CG (one block per small chain, 4-block "
                                    "clusters for 128x128 chains)",
                          "achieved": round(sach, 1), "peak": round(rates["smem_read_gbs"], 1),
                          "unit": "GB/s", "frac": round(sach / rates["smem_read_gbs"], 4),
                          "peak_source": "measured in this run (sm_peak_smem_read)",
-                         "bytes_per_site_iter": SMEM_BYTES_PER_SITE_ITER,
+                         "bytes_per_site_iter": SMEM_BYTES_COLUMN,
                          "hbm_equivalent": {"achieved": round(ach, 1), "peak": hbm,
                                             "frac": round(ach / hbm, 4),
                                             "bytes_per_site_iter": bps, "peak_source": src}},
