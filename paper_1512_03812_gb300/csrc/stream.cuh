@@ -86,7 +86,14 @@ __device__ __forceinline__ float ddagd_stream_walk(float4* ring, const ChainInfo
   const bool out0 = s0 >= 2 && s0 - 2 < ncols, out1 = s0 >= 1 && s0 - 1 < ncols;
   const int nrows = TT + 4;
   const int trows = T - ts;  // strip rows past this are outside the lattice
-  const float diag = (float)(2.0 + ci.m0);
+  // the walk carries 2 D in (2 diag in - hop, one FMA per component) and
+  // forms 4 D^dag D in the same way; the powers of two are exact, and the
+  // result and |D in|^2 are scaled once at the end
+  const float diag2 = (float)(2.0 * (2.0 + ci.m0));
+  auto twice_d = [&](const Sp<float>& v, const Sp<float>& h) {
+    return Sp<float>{{fmaf(diag2, v.a.re, -h.a.re), fmaf(diag2, v.a.im, -h.a.im)},
+                     {fmaf(diag2, v.b.re, -h.b.re), fmaf(diag2, v.b.im, -h.b.im)}};
+  };
 
   // step i reads window row i (down) or nrows - 1 - i (up); window row w is
   // lattice row ts - 2 + w
@@ -155,8 +162,8 @@ __device__ __forceinline__ float ddagd_stream_walk(float4* ring, const ChainInfo
         const Sp<float> h1 = hop_sum<false, float>(right, in_[p1][0], in_[tp][1], in_[tm][1], ux1,
                                                    ux0, {U_[p1][1].z, U_[p1][1].w},
                                                    {U_[tm][1].z, U_[tm][1].w});
-        D_[p1][0] = diag * in_[p1][0] - 0.5f * h0;
-        D_[p1][1] = diag * in_[p1][1] - 0.5f * h1;
+        D_[p1][0] = twice_d(in_[p1][0], h0);
+        D_[p1][1] = twice_d(in_[p1][1], h1);
         const int r = UP ? TT + 2 - i : i - 3;  // strip row of this D
         if (NORM && r >= 0 && r < TT && r < trows) {
           if (out0) nrm += norm2(D_[p1][0]);
@@ -183,11 +190,11 @@ __device__ __forceinline__ float ddagd_stream_walk(float4* ring, const ChainInfo
         if (r < trows) {
           const long long ro = (long long)L * (ts + r) + xs - 2 + s0;
           if (out0) {
-            const Sp<float> o = diag * D_[p2][0] - 0.5f * h0;
+            const Sp<float> o = 0.25f * twice_d(D_[p2][0], h0);
             out4[ro] = make_float4(o.a.re, o.a.im, o.b.re, o.b.im);
           }
           if (out1) {
-            const Sp<float> o = diag * D_[p2][1] - 0.5f * h1;
+            const Sp<float> o = 0.25f * twice_d(D_[p2][1], h1);
             out4[ro + 1] = make_float4(o.a.re, o.a.im, o.b.re, o.b.im);
           }
         }
@@ -195,7 +202,7 @@ __device__ __forceinline__ float ddagd_stream_walk(float4* ring, const ChainInfo
     }
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
-  return nrm;
+  return 0.25f * nrm;
 }
 
 // One entry {chain, xs, ts, dir} of the strip table: dir 1 walks down, 2 up,
