@@ -77,10 +77,10 @@ NCU_CAPTURES = {
                     "paper_1512_03812_gb300/csrc/common.cuh": "078132e7c68d198a"},
         "dram_bytes_per_launch": 84524800 + 36106496},
     "k_ddagd_stream": {
-        "sources": {"paper_1512_03812_gb300/csrc/stream.cuh": "8cfb0bc8bcfed0e2",
+        "sources": {"paper_1512_03812_gb300/csrc/stream.cuh": "3879e8e6b89ccdfc",
                     "paper_1512_03812_gb300/csrc/ddagd.cu": "0cc3a39f4068c6ef",
                     "paper_1512_03812_gb300/csrc/common.cuh": "1d7d22c0e0d74bdf"},
-        "dram_bytes_per_launch": 134648064 + 28383488},
+        "dram_bytes_per_launch": 134553856 + 27633408},
 }
 
 

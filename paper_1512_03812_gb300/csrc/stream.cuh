@@ -119,11 +119,14 @@ __device__ __forceinline__ float ddagd_stream_walk(float4* ring, const ChainInfo
   for (int k = 0; k < kSStages - 1; ++k) issue();
 
   // three-row register rings, slot = step mod 3: at step i, `cur` holds the
-  // row just read, p1 the one before it in walk order, p2 the one before that
+  // row just read, p1 the one before it in walk order, p2 the one before that.
+  // Walking up, the links of row i are taken at step i (D on row i - 1 needs
+  // U_t of the row below it, row i).  Walking down they are taken one step
+  // later, so that slot `cur` still holds the links of row i - 3, whose U_t
+  // D^dag on row i - 2 needs.
   Sp<float> in_[3][2], D_[3][2];
   float4 U_[3][2] = {};  // (Ux.re, Ux.im, Ut.re, Ut.im) of the lane's two sites
   Cx<float> uxl[3];      // U_x of the site left of 2 lane, per row
-  Cx<float> utm3[2];     // walking down: U_t of the row read three steps ago
   float nrm = 0.f;
 #pragma unroll 1
   for (int i0 = 0; i0 < nrows; i0 += 3) {
@@ -132,18 +135,23 @@ __device__ __forceinline__ float ddagd_stream_walk(float4* ring, const ChainInfo
       const int i = i0 + ph;
       if (i >= nrows) break;
       const int cur = ph, p1 = (ph + 2) % 3, p2 = (ph + 1) % 3;
+      if (!UP && i >= 1) {
+        // links of row i - 1, before the copy of this step reuses its stage
+        const float4* sp = ring + ((i - 1) % kSStages) * (2 * kSW);
+        U_[p1][0] = sp[kSW + sswz(s0)];
+        U_[p1][1] = sp[kSW + sswz(s0 + 1)];
+        __syncwarp();
+      }
       issue();
       asm volatile("cp.async.wait_group %0;\n" ::"n"(kSStages - 1) : "memory");
       __syncwarp();
       const float4* st = ring + (i % kSStages) * (2 * kSW);
-      if (!UP) {
-        utm3[0] = {U_[cur][0].z, U_[cur][0].w};
-        utm3[1] = {U_[cur][1].z, U_[cur][1].w};
-      }
       in_[cur][0] = f4sp(st[sswz(s0)]);
       in_[cur][1] = f4sp(st[sswz(s0 + 1)]);
-      U_[cur][0] = st[kSW + sswz(s0)];
-      U_[cur][1] = st[kSW + sswz(s0 + 1)];
+      if (UP) {
+        U_[cur][0] = st[kSW + sswz(s0)];
+        U_[cur][1] = st[kSW + sswz(s0 + 1)];
+      }
       __syncwarp();
       if (i >= 2) {
         // D on row p1; its t + 1 and t - 1 neighbours are rows cur and p2
@@ -180,8 +188,9 @@ __device__ __forceinline__ float ddagd_stream_walk(float4* ring, const ChainInfo
                                       D_[p2][1].b.im);
         const Sp<float> left = f4sp(shfl_up4(d1)), right = f4sp(shfl_down4(d0));
         const Cx<float> ux0 = {U_[p2][0].x, U_[p2][0].y}, ux1 = {U_[p2][1].x, U_[p2][1].y};
-        const Cx<float> utm0 = UP ? Cx<float>{U_[p1][0].z, U_[p1][0].w} : utm3[0];
-        const Cx<float> utm1 = UP ? Cx<float>{U_[p1][1].z, U_[p1][1].w} : utm3[1];
+        const int um = UP ? p1 : cur;  // the row below row p2
+        const Cx<float> utm0 = {U_[um][0].z, U_[um][0].w};
+        const Cx<float> utm1 = {U_[um][1].z, U_[um][1].w};
         const Sp<float> h0 = hop_sum<true, float>(D_[p2][1], left, D_[tp][0], D_[tm][0], ux0,
                                                   uxl[p2], {U_[p2][0].z, U_[p2][0].w}, utm0);
         const Sp<float> h1 = hop_sum<true, float>(right, D_[p2][0], D_[tp][1], D_[tm][1], ux1, ux0,
