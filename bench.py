@@ -642,12 +642,14 @@ PAPER = {
                ("five_stage_fg", "exact", 0.0550, 10, 370),
                ("five_stage_fg", "shifted", 0.0540, 8, 290),
                ("nested_fg", "exact", 0.0560, 8, 285),
-               ("adapted_nested_fg", "exact", 0.0560, 8, 285)],
+               ("adapted_nested_fg", "exact", 0.0560, 8, 285),
+               ("eleven_stage", "exact", 0.0625, 12, 384)],
     # |Delta H| against h (Fig. 1) for every integrator
     "scan_h": (0.0125, 0.025, 0.05, 0.1),
     "scan": [("leapfrog", "exact"), ("nested_leapfrog", "exact"), ("five_stage", "exact"),
              ("nested_five_stage", "exact"), ("five_stage_fg", "exact"),
-             ("five_stage_fg", "shifted"), ("nested_fg", "exact"), ("adapted_nested_fg", "exact")],
+             ("five_stage_fg", "shifted"), ("nested_fg", "exact"), ("adapted_nested_fg", "exact"),
+             ("eleven_stage", "exact")],
 }
 
 
@@ -713,7 +715,7 @@ def run_paper(args):
         return {"scheme": scheme, "fg": fg, "h": round(Wp["tau"] / n, 6), "n": n,
                 "M": Wp["M"] if "nested" in scheme else None,
                 "acceptance": round(float(np.mean(acc)), 4),
-                "acceptance_expected": round(float(np.mean(np.minimum(1.0, np.exp(-dH[ok])))), 4),
+                "acceptance_expected": round(float(np.mean(np.exp(np.minimum(0.0, -dH[ok])))), 4),
                 "median_abs_dH": float(np.median(a)),
                 "mean_abs_dH_stable": float(stable.mean()) if len(stable) else None,
                 "err_abs_dH_stable":

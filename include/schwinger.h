@@ -81,6 +81,8 @@ extern "C" {
 #define SM_NESTED_FIVE_STAGE 4   /* Eq. 5stage_multi */
 #define SM_NESTED_FG 5           /* Eq. 5stage_multi_fg (C_FF outside, C_GG inside) */
 #define SM_ADAPTED_NESTED_FG 6   /* Eq. ad_5stage_multi_fg (C_FF outside, leapfrog inside) */
+#define SM_ELEVEN_STAGE 7        /* Eq. 11_stage, with the weights of Eq. (71) of Omelyan,
+                                    Mryglod and Folk (2003) that the paper cites */
 
 /* how a force-gradient kick obtains C */
 #define SM_FG_EXACT 0    /* exact C via one extra CG (Eq. CFF, Eq. Z12) */

@@ -82,6 +82,37 @@ def five_stage_fg(st: State, h: float, fg: str = "exact", **_) -> None:
     kick(st, h / 6, "full")
 
 
+# The four weights of the 11-stage decomposition (Eq. 11_stage), which the
+# paper takes from Eq. (71) of Omelyan, Mryglod and Folk (2003): sigma and
+# lambda weight the force, eta and theta the drift.  They satisfy the two
+# fourth-order conditions of the symmetric composition (the coefficients of
+# [A,[A,B]] and [B,[B,A]] in log Delta_11 vanish; tests/test_oracle.py checks
+# this with a truncated Baker-Campbell-Hausdorff expansion).
+OMELYAN_11 = {"sigma": 0.08398315262876693, "eta": 0.2539785108410595,
+              "lam": 0.6822365335719091, "theta": -0.03230286765269967}
+
+
+def eleven_stage(st: State, h: float, **_) -> None:
+    """Delta_11(h) (Eq. 11_stage): force weights sigma, lambda,
+    (1 - 2 (lambda + sigma)) / 2 (twice), lambda, sigma; drift weights eta,
+    theta, 1 - 2 (theta + eta), theta, eta, interleaved as printed."""
+    w = OMELYAN_11
+    sg, et, lm, th = w["sigma"], w["eta"], w["lam"], w["theta"]
+    mid_b = (1 - 2 * (lm + sg)) / 2
+    mid_a = 1 - 2 * (th + et)
+    kick(st, sg * h, "full")
+    drift(st, et * h)
+    kick(st, lm * h, "full")
+    drift(st, th * h)
+    kick(st, mid_b * h, "full")
+    drift(st, mid_a * h)
+    kick(st, mid_b * h, "full")
+    drift(st, th * h)
+    kick(st, lm * h, "full")
+    drift(st, et * h)
+    kick(st, sg * h, "full")
+
+
 # ---------------------------------------------------------- nested schemes --
 
 def inner_leapfrog(st: State, h: float, M: int) -> None:
@@ -149,6 +180,7 @@ SCHEMES = {
     "nested_five_stage": nested_five_stage,
     "nested_fg": nested_fg,
     "adapted_nested_fg": adapted_nested_fg,
+    "eleven_stage": eleven_stage,
 }
 
 # Omelyan's second-order minimum-norm weight (Omelyan, Mryglod and Folk 2002),

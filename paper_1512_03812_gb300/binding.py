@@ -34,6 +34,7 @@ SCHEMES = {
     "nested_five_stage": 4,
     "nested_fg": 5,
     "adapted_nested_fg": 6,
+    "eleven_stage": 7,
 }
 FG_EXACT, FG_SHIFTED = 0, 1
 PARTS = {"gauge": PART_GAUGE, "fermion": PART_FERMION, "full": PART_FULL}

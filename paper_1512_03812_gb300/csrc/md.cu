@@ -131,7 +131,7 @@ static void inner_fg(std::vector<Op>& o, double h, int M) {
 }
 
 // The operations of one step of size h, written as the compositions of
-// Sec. 2 (Eq. leap, 5stage, 5stage_fg, leap_multi, 5stage_multi,
+// Sec. 2 (Eq. leap, 5stage, 5stage_fg, 11_stage, leap_multi, 5stage_multi,
 // 5stage_multi_fg, ad_5stage_multi_fg).
 static int build_step(std::vector<Op>& o, const sm_md_params& md, double h) {
   const int F = SM_PART_FULL, Fe = SM_PART_FERMION;
@@ -183,6 +183,20 @@ static int build_step(std::vector<Op>& o, const sm_md_params& md, double h) {
       inner_lf(o, h / 2, M);
       o.push_back({OP_KICK, Fe, h / 6});
       return SM_OK;
+    case SM_ELEVEN_STAGE: {
+      // force weights s, l, (1 - 2 (l + s)) / 2 (twice), l, s; drift weights
+      // e, t, 1 - 2 (t + e), t, e (Eq. 11_stage; the weights are those of
+      // Eq. (71) of Omelyan, Mryglod and Folk, 2003, cited by the paper)
+      const double s = 0.08398315262876693, e = 0.2539785108410595;
+      const double l = 0.6822365335719091, t = -0.03230286765269967;
+      const double mb = 0.5 * (1.0 - 2.0 * (l + s)), ma = 1.0 - 2.0 * (t + e);
+      const double kw[6] = {s, l, mb, mb, l, s}, dw[5] = {e, t, ma, t, e};
+      for (int k = 0; k < 6; ++k) {
+        o.push_back({OP_KICK, F, kw[k] * h});
+        if (k < 5) o.push_back({OP_DRIFT, 0, dw[k] * h});
+      }
+      return SM_OK;
+    }
     default:
       return fail(SM_ERR_ARG, "unknown scheme %d", md.scheme);
   }
@@ -202,7 +216,7 @@ static void merge(std::vector<Op>& o) {
 
 static int check_md(const sm_md_params* md) {
   if (!md) return fail(SM_ERR_ARG, "md params are NULL");
-  if (md->scheme < SM_LEAPFROG || md->scheme > SM_ADAPTED_NESTED_FG)
+  if (md->scheme < SM_LEAPFROG || md->scheme > SM_ELEVEN_STAGE)
     return fail(SM_ERR_ARG, "unknown scheme %d", md->scheme);
   if (md->M < 1) return fail(SM_ERR_ARG, "M = %d < 1", md->M);
   if (md->fg != SM_FG_EXACT && md->fg != SM_FG_SHIFTED) return fail(SM_ERR_ARG, "bad fg mode");

@@ -235,7 +235,7 @@ def test_shifted_force_matches_force_gradient_to_fourth_order():
 # ---------------------------------------------------------------- schemes --
 
 ALL = [("leapfrog", 1), ("five_stage", 1), ("five_stage_fg", 1), ("nested_leapfrog", 3),
-       ("nested_five_stage", 3), ("nested_fg", 2), ("adapted_nested_fg", 2)]
+       ("nested_five_stage", 3), ("nested_fg", 2), ("adapted_nested_fg", 2), ("eleven_stage", 1)]
 
 
 def _state(lat, q, phi, tol=1e-14, seed=2):
@@ -297,6 +297,7 @@ def _dH_slope(scheme, M, fg="exact", ns=(4, 8, 16), tau=0.5):
     ("adapted_nested_fg", lambda n: 2 * n * n, "exact", 4),
     ("adapted_nested_fg", lambda n: 2 * n * n, "shifted", 4),
     ("adapted_nested_fg", 1, "exact", 2),
+    ("eleven_stage", 1, "exact", 4),
 ])
 def test_delta_H_order(scheme, M, fg, order):
     s = _dH_slope(scheme, M, fg, ns=(5, 10) if callable(M) else (4, 8, 16))
@@ -356,3 +357,51 @@ def test_creutz_equality_on_markov_chain():
     vals = np.array(vals)
     err = vals.std() / math.sqrt(len(vals))
     assert abs(vals.mean() - 1.0) < 3 * err + 1e-3, (vals.mean(), err)
+
+
+# ------------------------------------------- 11-stage weights, BCH check --
+
+def _free_log(seq, deg=5):
+    """log of a product of exponentials exp(c X) (X = 'a' or 'b') in the free
+    associative algebra truncated at degree `deg`: {word: coefficient}."""
+    def mul(x, y):
+        z = {}
+        for w1, c1 in x.items():
+            for w2, c2 in y.items():
+                if len(w1) + len(w2) <= deg:
+                    z[w1 + w2] = z.get(w1 + w2, 0.0) + c1 * c2
+        return z
+    prod = {"": 1.0}
+    for letter, c in seq:
+        prod = mul(prod, {letter * k: c ** k / math.factorial(k) for k in range(deg + 1)})
+    z = {w: c for w, c in prod.items() if w}
+    out, power = {}, {"": 1.0}
+    for k in range(1, deg + 1):
+        power = mul(power, z)
+        for w, c in power.items():
+            out[w] = out.get(w, 0.0) + (-1) ** (k + 1) * c / k
+    return out
+
+
+def _eleven_stage_seq(sigma, eta, lam, theta):
+    """Eq. 11_stage as a word of exponentials: b = the force flow, a = drift."""
+    mb, ma = (1 - 2 * (lam + sigma)) / 2, 1 - 2 * (theta + eta)
+    return [("b", sigma), ("a", eta), ("b", lam), ("a", theta), ("b", mb), ("a", ma),
+            ("b", mb), ("a", theta), ("b", lam), ("a", eta), ("b", sigma)]
+
+
+def test_eleven_stage_weights_are_fourth_order():
+    """log Delta_11 = h (A + B) + O(h^5): the degree-1 part is a + b, degrees 2
+    and 4 vanish by symmetry, and the weights of Eq. (71) of Omelyan, Mryglod
+    and Folk (used by the paper for Eq. 11_stage) cancel both degree-3
+    commutators [a,[a,b]] = aab - 2 aba + baa and [b,[b,a]]: the coefficients
+    of the words aab and bba.  Moving one weight by 1e-6 breaks it."""
+    w = ig.OMELYAN_11
+    lg = _free_log(_eleven_stage_seq(w["sigma"], w["eta"], w["lam"], w["theta"]))
+    assert abs(lg["a"] - 1) < 1e-15 and abs(lg["b"] - 1) < 1e-15
+    for word, c in lg.items():
+        if len(word) in (2, 3, 4):
+            assert abs(c) < 1e-14, (word, c)
+    assert max(abs(c) for word, c in lg.items() if len(word) == 5) > 1e-5  # not sixth order
+    bad = _free_log(_eleven_stage_seq(w["sigma"] + 1e-6, w["eta"], w["lam"], w["theta"]))
+    assert max(abs(bad["aab"]), abs(bad["bba"])) > 1e-8
