@@ -854,8 +854,11 @@ static cudaError_t launch_cluster(Kern kern, int nch, int nt, size_t smem, cudaS
 
 int chain_cg_prepare(const sm_lattice* L, const sm_cg_params& cg) {
   if (cg.prec != SM_MIXED) return SM_OK;
-  int vmax = 0;
-  for (const ChainInfo& ci : L->chains) vmax = ci.L * ci.T > vmax ? ci.L * ci.T : vmax;
+  // the one-block kernels hold chains of up to kChainMaxVolume sites; larger
+  // chains (128 x 128) take the 4-block cluster, whose size is fixed
+  int vmax = 1;
+  for (const ChainInfo& ci : L->chains)
+    if (ci.L * ci.T <= kChainMaxVolume && ci.L * ci.T > vmax) vmax = ci.L * ci.T;
   const int smem = 3 * vmax * (int)sizeof(float4);
   cudaError_t e = cudaFuncSetAttribute(k_cg_chain_cluster<8, 256, 2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem / 2);

@@ -19,9 +19,12 @@ def torch():
     return t
 
 
-def test_graph_equals_eager_twice(torch):
+@pytest.mark.parametrize("dims", [[(64, 64), (16, 8), (8, 8)],
+                                  # a 128 x 128 chain takes the 4-block cluster kernel,
+                                  # the others the one-block kernels on a side stream
+                                  [(128, 128), (32, 32), (16, 16)]])
+def test_graph_equals_eager_twice(torch, dims):
     import paper_1512_03812_gb300 as P
-    dims = [(64, 64), (16, 8), (8, 8)]
     b = Batch(dims, [2.0, 1.5, 2.5], [0.24, 0.22, 0.23], seed=12)
     md = P.MD(scheme="adapted_nested_fg", tau=0.5, n=2, M=2,
               cg=P.CG(tol=1e-10, prec="mixed", delta=0.01), tol_action=1e-12)
