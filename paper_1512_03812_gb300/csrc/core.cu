@@ -54,6 +54,7 @@ size_t Ws::bytes(const sm_lattice* L) {
   b += 2 * align256(N * 32);           // U64, U64s
   b += 2 * align256(N * 16);           // U32, U32s
   b += 7 * align256(N * 16);           // link fields
+  b += align256(N * sizeof(double));   // plaquette sines
   b += align256(4 * nb * sizeof(double));
   b += align256(nc * sizeof(unsigned));
   b += align256(nc * sizeof(CgChain));
@@ -86,6 +87,7 @@ int Ws::carve(const sm_lattice* L, void* ws, size_t nbytes) {
   U32s = reinterpret_cast<float*>(take(N * 16));
   double** lf[] = {&F, &C, &F2, &qs, &qsave, &pw, &v};
   for (double** d : lf) *d = reinterpret_cast<double*>(take(N * 16));
+  sinp = reinterpret_cast<double*>(take(N * sizeof(double)));
   partials = reinterpret_cast<double*>(take(4 * nb * sizeof(double)));
   counters = reinterpret_cast<unsigned*>(take(nc * sizeof(unsigned)));
   cgc = reinterpret_cast<CgChain*>(take(nc * sizeof(CgChain)));
@@ -97,8 +99,10 @@ int Ws::carve(const sm_lattice* L, void* ws, size_t nbytes) {
   return SM_OK;
 }
 
-int Ctx::init(const sm_lattice* lat, void* ws, size_t nbytes, void* stream, sm_stats* stats) {
+int Ctx::init(const sm_lattice* lat, void* ws, size_t nbytes, void* stream, sm_stats* stats,
+               bool ws_required) {
   if (!lat) return fail(SM_ERR_ARG, "lattice is NULL");
+  if (ws_required && !ws) return fail(SM_ERR_ARG, "workspace is NULL");
   L = lat;
   g.chains = lat->d_chains;
   g.blk_chain = lat->d_blk_chain;
@@ -206,12 +210,10 @@ __device__ __forceinline__ GaugeNb gauge_nb(const Site& s) {
           at(s, xm, tp)};
 }
 
-// p -= eps F_G and/or Fout (=, or += if acc) F_G, with F_G = beta g of
-// Eq. force_gauge: F(n,x) = beta [sin th(n) - sin th(n-t)],
-//                  F(n,t) = beta [sin th(n-x) - sin th(n)].
-__global__ void __launch_bounds__(kBlock) k_gauge_kick(Geo g, const double* __restrict__ q,
-                                                       double* __restrict__ p, double eps,
-                                                       double* __restrict__ Fout, int acc) {
+// The same in one pass, three sines per site (for callers without a
+// workspace, which has the scratch field of the two-pass form).
+__global__ void __launch_bounds__(kBlock) k_gauge_kick_direct(Geo g, const double* __restrict__ q,
+                                                              double* __restrict__ Fout) {
   SITE_PROLOGUE
   if (!s.valid) return;
   const GaugeNb b = gauge_nb(s);
@@ -221,6 +223,33 @@ __global__ void __launch_bounds__(kBlock) k_gauge_kick(Geo g, const double* __re
   const double s0 = sin(plaq_angle(q0, qx, qt));
   const double s_mt = sin(plaq_angle(qmt, qxmt, q0));
   const double s_mx = sin(plaq_angle(qmx, q0, qmxt));
+  st_l2(Fout, s.n, make_double2(ci.beta * (s0 - s_mt), ci.beta * (s_mx - s0)));
+}
+
+// sin th(n) of the plaquette at every site (Eq. plaquette), one sine per
+// plaquette: the gauge kick below reads it at n, n - t and n - x, so the
+// FP64 sine (the kernel's cost on GB300's FP64 pipe) is taken once, not
+// three times, per plaquette.
+__global__ void __launch_bounds__(kBlock) k_plaq_sin(Geo g, const double* __restrict__ q,
+                                                     double* __restrict__ S) {
+  SITE_PROLOGUE
+  if (!s.valid) return;
+  const long long nx = at(s, xp1(s), s.t), nt = at(s, s.x, tp1(s));
+  S[s.n] = sin(plaq_angle(ld_l2(q, s.n), ld_l2(q, nx), ld_l2(q, nt)));
+}
+
+// p -= eps F_G and/or Fout (=, or += if acc) F_G, with F_G = beta g of
+// Eq. force_gauge: F(n,x) = beta [sin th(n) - sin th(n-t)],
+//                  F(n,t) = beta [sin th(n-x) - sin th(n)],
+// from S = sin th of k_plaq_sin.
+__global__ void __launch_bounds__(kBlock) k_gauge_kick(Geo g, const double* __restrict__ S,
+                                                       double* __restrict__ p, double eps,
+                                                       double* __restrict__ Fout, int acc) {
+  SITE_PROLOGUE
+  if (!s.valid) return;
+  const double s0 = __ldg(S + s.n);
+  const double s_mt = __ldg(S + at(s, s.x, tm1(s)));
+  const double s_mx = __ldg(S + at(s, xm1(s), s.t));
   const double2 F = make_double2(ci.beta * (s0 - s_mt), ci.beta * (s_mx - s0));
   if (Fout) {
     double2 o = F;
@@ -444,7 +473,15 @@ int launch_links(Ctx& c, const double* q, double* U64, float* U32) {
   return launched(c.st, "links");
 }
 int launch_gauge_kick(Ctx& c, const double* q, double* p, double eps, double* Fout, bool acc) {
-  k_gauge_kick<<<c.grid(), kBlock, 0, c.s>>>(c.g, q, p, eps, Fout, acc ? 1 : 0);
+  if (!c.w.sinp) {  // no workspace (sm_gauge_force): the one-pass form, F only
+    if (p || acc || !Fout) return fail(SM_ERR_ARG, "gauge kick without a workspace");
+    k_gauge_kick_direct<<<c.grid(), kBlock, 0, c.s>>>(c.g, q, Fout);
+    return launched(c.st, "gauge_kick_direct");
+  }
+  k_plaq_sin<<<c.grid(), kBlock, 0, c.s>>>(c.g, q, c.w.sinp);
+  const int rc = launched(c.st, "plaq_sin");
+  if (rc) return rc;
+  k_gauge_kick<<<c.grid(), kBlock, 0, c.s>>>(c.g, c.w.sinp, p, eps, Fout, acc ? 1 : 0);
   return launched(c.st, "gauge_kick");
 }
 int launch_fermion_kick(Ctx& c, const double* U64, const double* chi, const double* xi, double* p,
@@ -652,7 +689,7 @@ static bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 int sm_links(const sm_lattice* lat, const double* q, double* U64, float* U32, void* stream) {
   Ctx c;
-  int rc = c.init(lat, nullptr, 0, stream, nullptr);
+  int rc = c.init(lat, nullptr, 0, stream, nullptr, false);
   if (rc) return rc;
   if (!q || (!U64 && !U32)) return fail(SM_ERR_ARG, "sm_links: NULL field");
   if (!al16(q) || !al16(U64) || !al16(U32)) return fail(SM_ERR_ARG, "sm_links: unaligned field");
@@ -662,7 +699,7 @@ int sm_links(const sm_lattice* lat, const double* q, double* U64, float* U32, vo
 int sm_apply_D(const sm_lattice* lat, const void* U, const void* in, void* out, int dagger,
                int prec, void* stream) {
   Ctx c;
-  int rc = c.init(lat, nullptr, 0, stream, nullptr);
+  int rc = c.init(lat, nullptr, 0, stream, nullptr, false);
   if (rc) return rc;
   if (!U || !in || !out) return fail(SM_ERR_ARG, "sm_apply_D: NULL field");
   if (!al16(U) || !al16(in) || !al16(out)) return fail(SM_ERR_ARG, "sm_apply_D: unaligned field");
@@ -681,7 +718,7 @@ int sm_apply_DdagD(const sm_lattice* lat, const void* U, const void* in, void* o
   (void)ws;
   (void)ws_bytes;
   Ctx c;
-  int rc = c.init(lat, nullptr, 0, stream, nullptr);
+  int rc = c.init(lat, nullptr, 0, stream, nullptr, false);
   if (rc) return rc;
   if (!U || !in || !out) return fail(SM_ERR_ARG, "sm_apply_DdagD: NULL field");
   if (!al16(U) || !al16(in) || !al16(out))

@@ -83,6 +83,7 @@ struct Ws {
   float *U32, *U32s;
   // real link fields [N][2]
   double *F, *C, *F2, *qs, *qsave, *pw, *v;
+  double* sinp;  // [N] sine of the plaquette angle (gauge kick)
   // reductions
   double* partials;    // [4][nblocks]
   unsigned* counters;  // [nchains]
@@ -117,7 +118,9 @@ struct Ctx {
   bool deferred = false;
   bool capturing = false;  // inside a CUDA-graph capture (no profiling events)
 
-  int init(const sm_lattice* lat, void* ws, size_t nbytes, void* stream, sm_stats* stats);
+  // ws_required: the entry point takes a workspace (then ws may not be NULL)
+  int init(const sm_lattice* lat, void* ws, size_t nbytes, void* stream, sm_stats* stats,
+           bool ws_required = true);
   dim3 grid() const { return dim3((unsigned)L->nblocks); }
   int zero_counters();
   int sync();

@@ -297,7 +297,7 @@ extern "C" {
 
 int sm_gauge_force(const sm_lattice* lat, const double* q, double* F, void* stream) {
   Ctx c;
-  SM_TRY(c.init(lat, nullptr, 0, stream, nullptr));
+  SM_TRY(c.init(lat, nullptr, 0, stream, nullptr, false));
   SM_TRY(fields_ok({q, F}, "sm_gauge_force"));
   return launch_gauge_kick(c, q, nullptr, 0.0, F, false);
 }

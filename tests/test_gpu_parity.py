@@ -444,3 +444,19 @@ def test_nonfinite_input_is_reported(torch):
     assert np.array_equal(b.chain(qd, 1), b.chain(q, 1))
     with pytest.raises(P.SchwingerError):
         b.lat.hmc_trajectory(b.dev(q), b.dev(p), b.dev(eta), 0.5, md)
+
+
+def test_null_workspace_is_an_argument_error(torch):
+    """An entry point that takes a workspace refuses a NULL one (SM_ERR_ARG)
+    before launching anything; sm_gauge_force, which takes none, works."""
+    from paper_1512_03812_gb300 import binding as B
+    b = batch(torch)
+    qd = b.dev(b.q())
+    F = b.lat.field()
+    rc = B._LIB.sm_force(b.lat._h, B._ptr(qd), None, B.PARTS["gauge"], None, B._ptr(F), None, 0,
+                         None, B._stream())
+    assert rc == B.SM_ERR_ARG
+    assert "workspace" in B._LIB.sm_last_error().decode()
+    FG = b.lat.gauge_force(qd)
+    for c, ol in enumerate(b.olat):
+        assert rel_err(b.chain(FG, c), sw.gauge_force(ol, sw.links(b.chain(b.q(), c)))) < TOL64
