@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -325,6 +326,35 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_mixed(ChainCgArgs a) {
   }
 }
 
+// FP64 true residual in the column layout (reliable update): t64 = D x_hi,
+// then r = b - D^dag t64 on the thread's own strip of R rows of column x,
+// walking down the strip with a sliding window (t-neighbours and U_t(n - t)
+// from the rows before); x_hi, t64 and U64 are read at L2 (x_hi and t64 were
+// written in this kernel by other threads, before a barrier).
+struct ColWalk {
+  const double* U64;
+  long long off;
+  int L, T, x, xp, xm, t0;
+  double diag;
+  __device__ long long row(int t) const {
+    return off + (long long)(t < 0 ? t + T : (t >= T ? t - T : t)) * L;
+  }
+  // (D or D^dag) f at row t0 + j, given f at rows t0 + j - 1 (fm), t0 + j
+  // (fc), t0 + j + 1 (fn) and U_t at row t0 + j - 1 (utm); returns U_t of
+  // row t0 + j in utm
+  template <bool DAG>
+  __device__ Sp<double> site(const double* f, int j, const Sp<double>& fm, const Sp<double>& fc,
+                             const Sp<double>& fn, Cx<double>& utm) const {
+    const long long rw = row(t0 + j);
+    const Lk<double> u = ld_lk(U64, rw + x);
+    const Sp<double> o = hop_sum<DAG, double>(ld_sp_cg(f, rw + xp), ld_sp_cg(f, rw + xm), fn, fm,
+                                              u.x, ld_lk(U64, rw + xm).x, u.t, utm);
+    utm = u.t;
+    return diag * fc - 0.5 * o;
+  }
+};
+
+
 // Column layout for chains whose shape matches the block: thread tid owns
 // column x = tid % L and the R consecutive rows t0 .. t0 + R - 1 of row block
 // tid / L.  D and D^dag walk down the column with a sliding window, so the
@@ -463,14 +493,37 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_col(ChainCgArgs a) {
         xv[j] = {{0.f, 0.f}, {0.f, 0.f}};
       }
       __syncthreads();
-      const double* r64 = a.r64;
-      const int lshift = (L & (L - 1)) == 0 ? __ffs(L) - 1 : -1;
-      rr_true = true_residual(a, ci, lshift, redd, [&](int, int l, const Sp<double>& r) {
-        st_sp(const_cast<double*>(r64), ci.off + l, r);
-      });
-      __syncthreads();
+      {
+        const ColWalk cw{a.U64, ci.off, L, T, x, xp, xm, t0, 2.0 + ci.m0};
+        // t64 = D x_hi down the strip
+        Sp<double> fm = ld_sp_cg(a.x, cw.row(t0 - 1) + x), fc = ld_sp_cg(a.x, cw.row(t0) + x);
+        Cx<double> utm = ld_lk(a.U64, cw.row(t0 - 1) + x).t;
+#pragma unroll 1
+        for (int j = 0; j < R; ++j) {
+          const Sp<double> fn = ld_sp_cg(a.x, cw.row(t0 + j + 1) + x);
+          st_sp(a.t64, cw.row(t0 + j) + x, cw.site<false>(a.x, j, fm, fc, fn, utm));
+          fm = fc;
+          fc = fn;
+        }
+        __syncthreads();
+        // r = b - D^dag t64, into registers (FP32) and |r|^2 (FP64)
+        double v = 0.0;
+        fm = ld_sp_cg(a.t64, cw.row(t0 - 1) + x);
+        fc = ld_sp_cg(a.t64, cw.row(t0) + x);
+        utm = ld_lk(a.U64, cw.row(t0 - 1) + x).t;
 #pragma unroll
-      for (int j = 0; j < R; ++j) rv[j] = to_flt(ld_sp_cg(a.r64, ci.off + x + (t0 + j) * L));
+        for (int j = 0; j < R; ++j) {
+          const Sp<double> fn = ld_sp_cg(a.t64, cw.row(t0 + j + 1) + x);
+          const Sp<double> r =
+              ld_sp(a.b, cw.row(t0 + j) + x) - cw.site<true>(a.t64, j, fm, fc, fn, utm);
+          v += norm2(r);
+          rv[j] = to_flt(r);
+          fm = fc;
+          fc = fn;
+          asm volatile("" ::: "memory");  // one row's loads at a time (registers)
+        }
+        rr_true = cta_sum(v, redd);
+      }
       ++updates;
       if (!isfinite(rr_true)) {
         flags |= 2;
@@ -485,7 +538,10 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_col(ChainCgArgs a) {
       rr = (float)rr_true;
       rmax = rr;
     }
-    __syncthreads();  // ts and ps reads of this iteration are done
+    // no barrier here: the next p update writes only the thread's own sites
+    // of ps, and the next D stage's writes of ts follow that update's barrier;
+    // every read of ts and of neighbouring ps in this iteration precedes the
+    // barrier inside the |r|^2 sum above
   }
   if (threadIdx.x == 0) {
     CgChain* cc = a.cgc + c;
@@ -887,12 +943,14 @@ bool chain_cg_selected(const sm_lattice* L, const sm_cg_params& cg) {
   return cg.algo == SM_CG_CHAIN ? fits : (cg.algo == SM_CG_AUTO && fits);
 }
 
-// Deferred mode: acc[c] |= flags, acc[nchains + c] += iterations.
+// Deferred mode: acc[c] |= flags, acc[nchains + c] += iterations,
+// acc[2 nchains + c] += reliable updates.
 __global__ void k_cg_accumulate(const CgChain* __restrict__ cgc, int* acc, int nchains) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nchains) return;
   acc[c] |= cgc[c].flags;
   acc[nchains + c] += cgc[c].iters;
+  acc[2 * nchains + c] += cgc[c].need_update;  // the chain kernels' update count
 }
 
 int chain_cg_accumulate(Ctx& c) {

@@ -90,7 +90,7 @@ struct Ws {
   CgChain* cgc;        // [nchains]
   double* out;         // [8][nchains]
   int* flags;          // [nchains] per-chain masks
-  int* acc;            // [2][nchains] accumulated CG flags and iterations (deferred mode)
+  int* acc;            // [3][nchains] accumulated CG flags, iterations, reliable updates (deferred)
   int* n_active;       // [1]
   int* h_n_active;     // not in ws: pinned host word (see Ctx)
 

@@ -438,7 +438,7 @@ static int hmc_enqueue(Ctx& c, double* q, const double* p0, const double* eta,
   sm_cg_params cgH = cg;  // the S_F solves of H
   if (md.tol_action > 0.0) cgH.tol = md.tol_action;
   double* out = c.w.out;
-  if (c.deferred) SM_CU(cudaMemsetAsync(c.w.acc, 0, 2 * sizeof(int) * nc, c.s));
+  if (c.deferred) SM_CU(cudaMemsetAsync(c.w.acc, 0, 3 * sizeof(int) * nc, c.s));
   SM_TRY(make_links(c, q, c.w.U64, c.w.U32, cg));
   SM_TRY(launch_dslash<double>(c, c.w.U64, eta, c.w.phi, true, nullptr, 0.0));
   SM_CU(cudaMemcpyAsync(c.w.qsave, q, lbytes, cudaMemcpyDeviceToDevice, c.s));
@@ -458,7 +458,7 @@ static int hmc_finish(Ctx& c, double* q, const double* u, double* dH, double* H0
   const int nc = c.L->nchains;
   const size_t lbytes = sizeof(double) * 2 * (size_t)c.L->N;
   std::vector<double> h(6 * (size_t)nc);
-  std::vector<int> acc(2 * (size_t)nc, 0);
+  std::vector<int> acc(3 * (size_t)nc, 0);
   SM_CU(cudaMemcpyAsync(h.data(), c.w.out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c.s));
   if (c.deferred)
     SM_CU(cudaMemcpyAsync(acc.data(), c.w.acc, sizeof(int) * acc.size(), cudaMemcpyDeviceToHost, c.s));
@@ -468,6 +468,7 @@ static int hmc_finish(Ctx& c, double* q, const double* u, double* dH, double* H0
     for (int i = 0; i < nc; ++i) {
       c.chain_flags[i] = acc[i];
       c.st->chain_iterations += acc[nc + i];
+      c.st->reliable_updates += acc[2 * nc + i];
     }
     SM_TRY(profile_collect_deferred(c.L, acc.data() + nc));
   }
