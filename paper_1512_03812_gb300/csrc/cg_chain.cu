@@ -728,22 +728,34 @@ __global__ void __launch_bounds__(NT, (K == 2 && NT == 256 ? 2 : 1)) k_cg_chain_
         xv[j] = {{0.f, 0.f}, {0.f, 0.f}};
       }
       cl.sync();
-      const double dg = 2.0 + ci.m0;
-      const int lshift = (L & (L - 1)) == 0 ? __ffs(L) - 1 : -1;
-      for (int l = threadIdx.x; l < HV; l += NT) {
-        const Nb n = neighbours(l + (int)rank * HV, L, T, lshift);
-        st_sp(a.t64, ci.off + n.l, dslash_glob<false>(a.x, a.U64, ci.off, n, dg));
+      // t64 = D x_hi, then r = b - D^dag t64, down the thread's strip (its
+      // first row in the chain is rank H + t0); rows beyond this block's part
+      // are read from global memory like the others, after a cluster barrier
+      const ColWalk cw{a.U64, ci.off, L, T, x, xp, xm, (int)rank * H + t0, 2.0 + ci.m0};
+      Sp<double> fm = ld_sp_cg(a.x, cw.row(cw.t0 - 1) + x), fc = ld_sp_cg(a.x, cw.row(cw.t0) + x);
+      Cx<double> utm = ld_lk(a.U64, cw.row(cw.t0 - 1) + x).t;
+#pragma unroll 1
+      for (int j = 0; j < R; ++j) {
+        const Sp<double> fn = ld_sp_cg(a.x, cw.row(cw.t0 + j + 1) + x);
+        st_sp(a.t64, cw.row(cw.t0 + j) + x, cw.site<false>(a.x, j, fm, fc, fn, utm));
+        fm = fc;
+        fc = fn;
       }
       cl.sync();
       double v = 0.0;
+      fm = ld_sp_cg(a.t64, cw.row(cw.t0 - 1) + x);
+      fc = ld_sp_cg(a.t64, cw.row(cw.t0) + x);
+      utm = ld_lk(a.U64, cw.row(cw.t0 - 1) + x).t;
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        const int l = x + (t0 + j) * L + (int)rank * HV;
-        const Nb n = neighbours(l, L, T, lshift);
+        const Sp<double> fn = ld_sp_cg(a.t64, cw.row(cw.t0 + j + 1) + x);
         const Sp<double> r =
-            ld_sp(a.b, ci.off + l) - dslash_glob<true>(a.t64, a.U64, ci.off, n, dg);
+            ld_sp(a.b, cw.row(cw.t0 + j) + x) - cw.site<true>(a.t64, j, fm, fc, fn, utm);
         v += norm2(r);
         rv[j] = to_flt(r);
+        fm = fc;
+        fc = fn;
+        asm volatile("" ::: "memory");  // one row's loads at a time (registers)
       }
       rr_true = csumd(v);
       ++updates;
