@@ -135,3 +135,41 @@ def test_stream_ragged_batch_every_site(torch):
         r = b.chain(psi, c) - sw.apply_DdagD(ol, U, b.chain(x, c))
         assert np.linalg.norm(r) <= 1.0000001e-10 * np.linalg.norm(b.chain(psi, c))
     assert b.lat.check() == 0
+
+
+def test_bench_workload_sampled_chains(torch):
+    """The bench's launch configuration: 304 chains of 64 x 64 (beta 2,
+    kappa 0.26), the autotuned chain-resident kernel, one trajectory of
+    adapted nested FG (n 8, M 2, tau 1) with the mixed CG at 1e-10 (1e-12
+    for H) and reliable-update factor 1e-3.  Two sampled chains, one from
+    each wave of 152, against the oracle's FP64 trajectory at 1e-12: Delta H
+    to the solver tolerance, and the same decision wherever u is not within
+    1e-4 of exp(-Delta H)."""
+    import paper_1512_03812_gb300 as P
+    from oracle import integrators as ig
+    B, L = 304, 64
+    m0 = sw.kappa_to_m0(0.26)
+    lat = P.Lattice([L] * B, [L] * B, 2.0, m0)
+    # disordered but not hot: 0.3 x the seeded hot angles (CG converges in a
+    # few hundred iterations, as on the bench's thermalised chains)
+    q = np.concatenate([0.3 * I.hot_links(L, L, 400 + c) for c in range(B)])
+    p = np.concatenate([I.momenta(L, L, 700 + c) for c in range(B)])
+    eta = np.concatenate([I.noise(L, L, 900 + c) for c in range(B)])
+    u = I.uniforms(B, 33)
+    qd = torch.tensor(q, device="cuda")
+    U64, U32 = lat.links(qd)
+    cg = P.CG(tol=1e-10, maxit=20000, prec="mixed", delta=1e-3)
+    lat.autotune_cg(U64, U32, torch.tensor(eta, device="cuda"), cg)
+    md = P.MD(scheme="adapted_nested_fg", tau=1.0, n=8, M=2, fg="exact", cg=cg, tol_action=1e-12)
+    dH, H0, acc = lat.hmc_trajectory(qd, torch.tensor(p, device="cuda"),
+                                     torch.tensor(eta, device="cuda"), u, md)
+    V = L * L
+    ol = sw.Lattice(L, L, 2.0, m0)
+    for c in (7, 230):
+        sl = slice(c * V, (c + 1) * V)
+        r = ig.hmc_trajectory(ol, q[sl].reshape(L, L, 2), p[sl].reshape(L, L, 2),
+                              eta[sl].reshape(L, L, 2), u[c], "adapted_nested_fg", 1.0, 8, M=2,
+                              solver=sw.Solver(1e-12))
+        assert abs(dH[c] - r.dH) < 1e-6 * max(1.0, abs(r.dH)), (c, dH[c], r.dH)
+        if abs(u[c] - np.exp(-r.dH)) > 1e-4:
+            assert bool(acc[c]) == r.accepted
