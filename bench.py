@@ -48,6 +48,10 @@ WORKLOAD = {
 # writes p, t; kernel B reads t, U, p, x, r and writes x, r; 16 B each in
 # FP32, 32 B in FP64).
 CG_BYTES_PER_SITE_ITER = {"mixed": (3 + 2) * 16 + (5 + 2) * 16, "f64": (3 + 2) * 32 + (5 + 2) * 32}
+# The fused streaming iteration of large lattices (cg_tiled.cu): F reads r,
+# p_old, U and writes p, A p; x += alpha p_old in L2 (read and written back);
+# R reads r, A p and writes r.
+FUSED_CG_BYTES_PER_SITE_ITER = (3 + 2) * 16 + 2 * 16 + (2 + 1) * 16
 # Shared-memory bytes per site and iteration of the chain-resident FP32 CG
 # (cg_chain.cu), by kernel variant.  Strided layout (0): p update 2 x 16,
 # t = D p reads 5 p + 3 U and writes t (9 x 16), D^dag t reads 5 t + 3 U + p
@@ -640,12 +644,16 @@ def run_other(args):
                                             "bytes_per_site_iter": bps, "peak_source": src}},
                         **common)
     else:
+        # the 2048^2 lattice takes the fused streaming iteration: F reads r,
+        # p_old, U and writes p, A p (80 B), advances x in L2 (32 B of DRAM
+        # traffic), R reads r, A p and writes r (48 B)
+        fbps = FUSED_CG_BYTES_PER_SITE_ITER
+        fach = fbps * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
         roofline = dict({"bound": "hbm",
-                         "kernel": "tiled grid-wide CG iteration (k_cgt_p + k_cgt_ap_stream + "
-                                   "k_cgt_xr)",
-                         "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                         "frac": round(ach / hbm, 4), "peak_source": src,
-                         "bytes_per_site_iter": bps}, **common)
+                         "kernel": "fused streaming CG iteration (k_cgt_f + k_cgt_r)",
+                         "achieved": round(fach, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(fach / hbm, 4), "peak_source": src,
+                         "bytes_per_site_iter": fbps}, **common)
     print(json.dumps({
         "metric": "HMC trajectories/s", "value": round(B * args.steps / (ms / 1e3), 4),
         "unit": "trajectories/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,

@@ -21,7 +21,7 @@ struct ChainInfo {
   long long off;
   int blk0, nblk;  // site blocks of the chain
   int tb0, ntb;    // its tiles in the 64 x 16 tile table
-  int sb0, nsb;    // its blocks in the streaming D^dag D table
+  int sb0, nsb;    // its blocks in the fused CG iteration's strip table
   double beta, m0;
 };
 

@@ -662,6 +662,7 @@ int sm_lattice_destroy(sm_lattice* lat) {
   if (lat->ev_join) cudaEventDestroy(lat->ev_join);
   if (lat->d_tiles_big) cudaFree(lat->d_tiles_big);
   if (lat->d_stream) cudaFree(lat->d_stream);
+  if (lat->d_stream_cg) cudaFree(lat->d_stream_cg);
   if (lat->h_pinned) cudaFreeHost(lat->h_pinned);
   if (lat->ev[0]) cudaEventDestroy(lat->ev[0]);
   if (lat->ev[1]) cudaEventDestroy(lat->ev[1]);

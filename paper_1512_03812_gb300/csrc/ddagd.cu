@@ -157,6 +157,22 @@ static long long stream_blocks(const sm_lattice* lat, int TT) {
   return nb;
 }
 
+// The lowest strip height whose blocks all fit on the GPU at once (one wave)
+// for a kernel that holds `occ` blocks per SM; launches with fewer strips per
+// SM than that lose bandwidth.
+static int stream_height(const sm_lattice* lat, int nsm, int occ) {
+  const long long slots = (long long)nsm * occ;
+  int tmax = 0;
+  for (const ChainInfo& ci : lat->chains) tmax = std::max(tmax, ci.T);
+  int lo = 8, hi = std::max(8, tmax);
+  if (stream_blocks(lat, hi) > slots) return 32;  // more than one wave whatever the height
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if (stream_blocks(lat, mid) <= slots) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
 int stream_ranges(sm_lattice* lat) {
   // every chain must be wide enough that the 64-column windows waste little
   // (at most 30 % more columns than the lattice has)
@@ -164,55 +180,53 @@ int stream_ranges(sm_lattice* lat) {
   for (const ChainInfo& ci : lat->chains)
     if (10LL * kSW * ((ci.L + kSOut - 1) / kSOut) > 13LL * ci.L) lat->stream_ok = false;
   if (!lat->stream_ok) return SM_OK;
-  // the lowest strip height whose blocks all fit on the GPU at once (one
-  // wave); launches with fewer strips per SM than that lose bandwidth
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return fail(SM_ERR_CUDA, "device attribute");
-  const int occ = std::min(ddagd_stream_occupancy(), cgt_stream_occupancy());
-  if (occ <= 0) return fail(SM_ERR_CUDA, "streaming D^dag D: no occupancy");
-  const long long slots = (long long)nsm * occ;
-  int tmax = 0;
-  for (const ChainInfo& ci : lat->chains) tmax = std::max(tmax, ci.T);
-  int lo = 8, hi = std::max(8, tmax);
-  if (stream_blocks(lat, hi) > slots) {
-    lo = hi = 32;  // more than one wave whatever the height
-  }
-  while (lo < hi) {
-    const int mid = (lo + hi) / 2;
-    if (stream_blocks(lat, mid) <= slots) hi = mid; else lo = mid + 1;
-  }
-  lat->stream_tt = lo;
+  const int occ_d = ddagd_stream_occupancy(), occ_cg = cgt_fused_occupancy();
+  if (occ_d <= 0 || occ_cg <= 0) return fail(SM_ERR_CUDA, "streaming D^dag D: no occupancy");
+  // the D^dag D and the CG iteration keep their own strip tables: the CG
+  // kernel holds fewer blocks per SM (more registers, a larger ring)
+  lat->stream_tt = stream_height(lat, nsm, occ_d);
+  lat->nstream = (int)stream_blocks(lat, lat->stream_tt);
+  lat->stream_tt_cg = stream_height(lat, nsm, occ_cg);
   int first = 0;
   for (ChainInfo& ci : lat->chains) {
-    const long long strips =
-        (long long)((ci.L + kSOut - 1) / kSOut) * ((ci.T + lo - 1) / lo);
+    const long long strips = (long long)((ci.L + kSOut - 1) / kSOut) *
+                             ((ci.T + lat->stream_tt_cg - 1) / lat->stream_tt_cg);
     ci.sb0 = first;
     ci.nsb = (int)((strips + kSWarps - 1) / kSWarps);
     first += ci.nsb;
   }
-  lat->nstream = first;
+  lat->nstream_cg = first;
+  return SM_OK;
+}
+
+// {chain, xs, ts, dir} per warp, kSWarps per block and a chain's last block
+// padded with {chain, 0, 0, 0}; vertically adjacent strips walk in opposite
+// directions
+static int make_strips(const sm_lattice* lat, int TT, int4** d) {
+  std::vector<int4> t;
+  for (int c = 0; c < lat->nchains; ++c) {
+    const ChainInfo& ci = lat->chains[c];
+    const size_t first = t.size();
+    for (int y = 0, k = 0; y < ci.T; y += TT, ++k)
+      for (int x = 0; x < ci.L; x += kSOut) t.push_back(make_int4(c, x, y, 1 + (k & 1)));
+    while ((t.size() - first) % kSWarps) t.push_back(make_int4(c, 0, 0, 0));
+  }
+  cudaError_t e = cudaMalloc(d, sizeof(int4) * t.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(*d, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(SM_ERR_CUDA, "strip table: %s", cudaGetErrorString(e));
   return SM_OK;
 }
 
 static int build_stream_table(sm_lattice* lat) {
   if (!lat->stream_ok) return SM_OK;
-  std::vector<int4> t;
-  t.reserve((size_t)lat->nstream * kSWarps);
-  for (int c = 0; c < lat->nchains; ++c) {
-    const ChainInfo& ci = lat->chains[c];
-    const size_t first = t.size();
-    // vertically adjacent strips walk in opposite directions
-    for (int y = 0, k = 0; y < ci.T; y += lat->stream_tt, ++k)
-      for (int x = 0; x < ci.L; x += kSOut) t.push_back(make_int4(c, x, y, 1 + (k & 1)));
-    while ((t.size() - first) % kSWarps) t.push_back(make_int4(c, 0, 0, 0));
-  }
-  cudaError_t e = cudaMalloc(&lat->d_stream, sizeof(int4) * t.size());
-  if (e == cudaSuccess)
-    e = cudaMemcpy(lat->d_stream, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return fail(SM_ERR_CUDA, "strip table: %s", cudaGetErrorString(e));
-  return SM_OK;
+  const int rc = make_strips(lat, lat->stream_tt, &lat->d_stream);
+  if (rc) return rc;
+  return make_strips(lat, lat->stream_tt_cg, &lat->d_stream_cg);
 }
 
 // Tensor maps of `in` and U for TMA staging (single-chain lattices large

@@ -23,13 +23,16 @@ struct sm_lattice {
   int ntiles;
   int4* d_tiles_big;  // 64 x 16 tiles of its large-lattice FP32 form
   int ntiles_big;
-  // streaming FP32 D^dag D (stream.cuh): kSWarps strips {chain, xs, ts, 1}
+  // streaming FP32 D^dag D (stream.cuh): kSWarps strips {chain, xs, ts, dir}
   // per block ({chain, 0, 0, 0} pads a chain's last block), strips of
-  // stream_tt rows; stream_ok if every chain is wide enough for it
+  // stream_tt rows; stream_ok if every chain is wide enough for it.  The
+  // fused CG iteration has its own table (strips of stream_tt_cg rows;
+  // ChainInfo::sb0, nsb index its blocks).
   bool stream_ok;
-  int stream_tt;
-  int nstream;  // blocks
+  int stream_tt, stream_tt_cg;
+  int nstream, nstream_cg;  // blocks
   int4* d_stream;
+  int4* d_stream_cg;
   int cg_variant;     // chain-resident mixed CG kernel chosen by sm_autotune_cg (-1: default)
   // mixed batches: chains of at most 4096 sites (solved chain-resident on the
   // side stream) and the mask of the others (solved grid-wide)
@@ -70,6 +73,7 @@ struct CgChain {
   int flags;       // bit 0: maxit reached, bit 1: breakdown (p^dag A p <= 0)
   int par;         // which of the two search-direction buffers holds p
   int updates;     // grid-wide form: reliable updates done
+  double alpha_x;  // fused tiled form: x += alpha_x p still to be applied
 };
 
 // Scratch carved from the caller's workspace.
@@ -159,7 +163,7 @@ void big_tile_ranges(sm_lattice* lat);
 // form (before the chain table is uploaded).
 int stream_ranges(sm_lattice* lat);
 int ddagd_stream_occupancy();
-int cgt_stream_occupancy();
+int cgt_fused_occupancy();
 template <typename R>
 int launch_ddagd(Ctx& c, const R* U, const R* in, R* out);
 
@@ -183,8 +187,11 @@ int chain_cg_launch_list(Ctx& c, const double* U64, const float* U32, const doub
 // The tiled grid-wide mixed iteration (cg_tiled.cu) for batches of 2^18
 // sites or more: n iterations of P, AP, XR on r, x, p (in place), Ap.
 bool tiled_cg_applies(const sm_lattice* L);
-int tiled_cg_iterate(Ctx& c, const float* U32, float* r, float* x, float* p, float* Ap,
-                     double tol2, double delta2, int maxit, int n);
+int tiled_cg_iterate(Ctx& c, const float* U32, float* r, float* x, float* pa, float* pb,
+                     float* Ap, double tol2, double delta2, int maxit, int n);
+// Before a reliable update of the fused tiled form: x += alpha_x p for the
+// chains about to be updated (their pending update of the iterate).
+int tiled_cg_flush(Ctx& c, float* x, const float* pa, const float* pb);
 
 // Kernel times of deferred solves and their site-iterations (solver.cu);
 // call after the stream has been synchronised.

@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(Geo g, CgArgs<R> a) {
     cc->par = 0;
     cc->need_update = 0;
     cc->updates = 0;
+    cc->alpha_x = 0.0;
     cc->flags = 0;
     if (bb > 0.0 && isfinite(bb)) {
       cc->state = 1;
@@ -255,6 +256,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_res_r(Geo g, CgArgs<float> a, dou
     if (!all) {
       cc->need_update = 0;
       cc->updates += 1;
+      cc->alpha_x = 0.0;  // x (with any pending update) is now in xhi
       cc->rmax = rr;
       if (!isfinite(rr)) {
         cc->flags |= 2;
@@ -339,7 +341,7 @@ template <typename R>
 static int iterate(Ctx& c, CgArgs<R>& a, int n) {
   if (a.mixed && tiled_cg_applies(c.L))  // large batches: the tiled iteration
     return tiled_cg_iterate(c, (const float*)a.U, (float*)a.r, (float*)a.x, (float*)a.pa,
-                            (float*)a.t, a.tol2, a.delta2, a.maxit, n);
+                            (float*)a.pb, (float*)a.t, a.tol2, a.delta2, a.maxit, n);
   for (int k = 0; k < n; ++k) {
     k_cg_a<R><<<c.grid(), kBlock, 0, c.s>>>(c.g, a);
     int rc = launched(c.st, "cg_a");
@@ -352,6 +354,11 @@ static int iterate(Ctx& c, CgArgs<R>& a, int n) {
 }
 
 static int residual(Ctx& c, CgArgs<float>& a, double* xhi, const float* x, int all) {
+  if (!all && x && tiled_cg_applies(c.L) && c.L->stream_ok) {
+    // the fused tiled iteration leaves x += alpha p pending: apply it first
+    const int rc = tiled_cg_flush(c, a.x, a.pa, a.pb);
+    if (rc) return rc;
+  }
   k_cg_res_d<<<c.grid(), kBlock, 0, c.s>>>(c.g, a, xhi, x, all);
   int rc = launched(c.st, "cg_res_d");
   if (rc) return rc;

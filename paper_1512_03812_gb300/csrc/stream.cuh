@@ -32,6 +32,27 @@ constexpr int kSStages = 4;      // ring depth in rows
 constexpr int kSThreads = 32 * kSWarps;
 constexpr int kSRing = kSStages * 2 * kSW;  // float4 per warp: `in` then U per stage
 
+// The CG form of the walk (cg_tiled.cu): its input is the search direction
+// p = r + beta p_old, formed for every window site from r and p_old; the
+// strip's own sites also store p (into pnew) and take x += alpha_x p_old (the
+// previous iteration's update of the iterate, by reductions the warp does not
+// wait for).  The ring then holds r, U and p_old per row.
+struct CgFuse {
+  const float* pold;
+  float* pnew;
+  float* x;
+  float beta, alpha_x;
+};
+constexpr int kSRingCG = kSStages * 3 * kSW;  // float4 per warp in the CG form
+
+// *p += v in global memory without waiting for the result (a vector
+// reduction, performed at L2)
+__device__ __forceinline__ void red_add4s(float4* p, float4 v) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(p), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w)
+               : "memory");
+}
+
 // Ring slot of window site s: pairs of slots are swapped in every second
 // group of 8, so that a lane reading sites 2 l (or 2 l + 1) and the copies
 // writing sites l, l + 32 both touch 32 distinct banks per quarter-warp.
@@ -66,11 +87,12 @@ __device__ __forceinline__ float4 shfl_down4(float4 v) {
 // same time (at the start of both walks, or at the end of both) and the second
 // read finds them in L2.  Returns this lane's part of |D in|^2 over the
 // strip's own sites if NORM.  Call from all 32 lanes.
-template <bool NORM, bool UP>
+template <bool NORM, bool UP, bool CG = false>
 __device__ __forceinline__ float ddagd_stream_walk(float4* ring, const ChainInfo& ci, int xs,
                                                    int ts, int TT, const float* __restrict__ U,
                                                    const float* __restrict__ in,
-                                                   float* __restrict__ out) {
+                                                   float* __restrict__ out, const CgFuse& cgf) {
+  constexpr int NP = CG ? 3 : 2;  // planes per ring stage: in (or r), U, [p_old]
   const int lane = threadIdx.x & 31;
   const int L = ci.L, T = ci.T;
   const float4* in4 = reinterpret_cast<const float4*>(in) + ci.off;
@@ -99,14 +121,19 @@ __device__ __forceinline__ float ddagd_stream_walk(float4* ring, const ChainInfo
   // lattice row ts - 2 + w
   int tload = UP ? wrap(ts + TT + 1, T) : wrap(ts - 2, T);
   int iload = 0;
+  const float4* po4 = CG ? reinterpret_cast<const float4*>(cgf.pold) + ci.off : nullptr;
   auto issue = [&]() {
     if (iload < nrows) {
-      float4* st = ring + (iload % kSStages) * (2 * kSW);
+      float4* st = ring + (iload % kSStages) * (NP * kSW);
       const long long ro = (long long)L * tload;
       cp_async16s(st + sswz(lane), in4 + ro + cx0);
       cp_async16s(st + sswz(lane + 32), in4 + ro + cx1);
       cp_async16s(st + kSW + sswz(lane), U4 + ro + cx0);
       cp_async16s(st + kSW + sswz(lane + 32), U4 + ro + cx1);
+      if (CG) {
+        cp_async16s(st + 2 * kSW + sswz(lane), po4 + ro + cx0);
+        cp_async16s(st + 2 * kSW + sswz(lane + 32), po4 + ro + cx1);
+      }
       if (UP)
         tload = tload == 0 ? T - 1 : tload - 1;
       else
@@ -137,7 +164,7 @@ __device__ __forceinline__ float ddagd_stream_walk(float4* ring, const ChainInfo
       const int cur = ph, p1 = (ph + 2) % 3, p2 = (ph + 1) % 3;
       if (!UP && i >= 1) {
         // links of row i - 1, before the copy of this step reuses its stage
-        const float4* sp = ring + ((i - 1) % kSStages) * (2 * kSW);
+        const float4* sp = ring + ((i - 1) % kSStages) * (NP * kSW);
         U_[p1][0] = sp[kSW + sswz(s0)];
         U_[p1][1] = sp[kSW + sswz(s0 + 1)];
         __syncwarp();
@@ -145,9 +172,37 @@ __device__ __forceinline__ float ddagd_stream_walk(float4* ring, const ChainInfo
       issue();
       asm volatile("cp.async.wait_group %0;\n" ::"n"(kSStages - 1) : "memory");
       __syncwarp();
-      const float4* st = ring + (i % kSStages) * (2 * kSW);
+      const float4* st = ring + (i % kSStages) * (NP * kSW);
       in_[cur][0] = f4sp(st[sswz(s0)]);
       in_[cur][1] = f4sp(st[sswz(s0 + 1)]);
+      if (CG) {
+        // p = r + beta p_old on the window; the strip's own sites store p
+        // and add alpha_x p_old to x
+        const Sp<float> po0 = f4sp(st[2 * kSW + sswz(s0)]), po1 = f4sp(st[2 * kSW + sswz(s0 + 1)]);
+        in_[cur][0] = in_[cur][0] + cgf.beta * po0;
+        in_[cur][1] = in_[cur][1] + cgf.beta * po1;
+        const int sr = (UP ? nrows - 1 - i : i) - 2;  // strip row of the row read
+        if (sr >= 0 && sr < TT && sr < trows) {
+          const long long ro = (long long)L * (ts + sr) + xs - 2 + s0;
+          float4* pn4 = reinterpret_cast<float4*>(cgf.pnew) + ci.off;
+          float4* x4 = reinterpret_cast<float4*>(cgf.x) + ci.off;
+          const float ax = cgf.alpha_x;
+          if (out0) {
+            const Sp<float>& v = in_[cur][0];
+            pn4[ro] = make_float4(v.a.re, v.a.im, v.b.re, v.b.im);
+            if (ax != 0.f)
+              red_add4s(x4 + ro, make_float4(ax * po0.a.re, ax * po0.a.im, ax * po0.b.re,
+                                             ax * po0.b.im));
+          }
+          if (out1) {
+            const Sp<float>& v = in_[cur][1];
+            pn4[ro + 1] = make_float4(v.a.re, v.a.im, v.b.re, v.b.im);
+            if (ax != 0.f)
+              red_add4s(x4 + ro + 1, make_float4(ax * po1.a.re, ax * po1.a.im, ax * po1.b.re,
+                                                 ax * po1.b.im));
+          }
+        }
+      }
       if (UP) {
         U_[cur][0] = st[kSW + sswz(s0)];
         U_[cur][1] = st[kSW + sswz(s0 + 1)];
@@ -221,8 +276,24 @@ __device__ __forceinline__ float ddagd_stream_strip(float4* ring, const ChainInf
                                                     int4 s, int TT, const float* __restrict__ U,
                                                     const float* __restrict__ in,
                                                     float* __restrict__ out) {
-  if (s.w == 1) return ddagd_stream_walk<NORM, false>(ring, chains[s.x], s.y, s.z, TT, U, in, out);
-  if (s.w == 2) return ddagd_stream_walk<NORM, true>(ring, chains[s.x], s.y, s.z, TT, U, in, out);
+  const CgFuse none{};
+  if (s.w == 1)
+    return ddagd_stream_walk<NORM, false>(ring, chains[s.x], s.y, s.z, TT, U, in, out, none);
+  if (s.w == 2)
+    return ddagd_stream_walk<NORM, true>(ring, chains[s.x], s.y, s.z, TT, U, in, out, none);
+  return 0.f;
+}
+
+// The CG form of one strip (see CgFuse): Ap = D^dag D p with p = r + beta
+// p_old, returning this lane's part of |D p|^2.
+__device__ __forceinline__ float ddagd_stream_strip_cg(float4* ring, const ChainInfo* chains,
+                                                       int4 s, int TT, const float* __restrict__ U,
+                                                       const float* __restrict__ r,
+                                                       float* __restrict__ Ap, const CgFuse& f) {
+  if (s.w == 1)
+    return ddagd_stream_walk<true, false, true>(ring, chains[s.x], s.y, s.z, TT, U, r, Ap, f);
+  if (s.w == 2)
+    return ddagd_stream_walk<true, true, true>(ring, chains[s.x], s.y, s.z, TT, U, r, Ap, f);
   return 0.f;
 }
 
