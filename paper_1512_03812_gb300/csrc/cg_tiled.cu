@@ -40,6 +40,7 @@ struct TiledArgs {
   unsigned* counters;
   int* n_active;
   int* err;
+  const unsigned char* grid_mask;  // hybrid solves: 0 for chains solved chain-resident
   double tol2, delta2;
   int maxit;
 };
@@ -280,6 +281,7 @@ __global__ void __launch_bounds__(kSThreads) k_cgt_r(TiledArgs a) {
 // x += alpha_x p for the chains about to take a reliable update
 __global__ void __launch_bounds__(kBlock) k_cgt_xflush(TiledArgs a) {
   const int c = a.g.blk_chain[blockIdx.x];
+  if (a.grid_mask && !a.grid_mask[c]) return;
   const CgChain* cc = a.cgc + c;
   if (!cc->need_update || cc->alpha_x == 0.0) return;
   const ChainInfo ci = a.g.chains[c];
@@ -339,9 +341,11 @@ __global__ void __launch_bounds__(kBlock) k_cgt_xr(TiledArgs a) {
 
 bool tiled_cg_applies(const sm_lattice* L) { return L->N >= (1 << 18); }
 
-int tiled_cg_flush(Ctx& c, float* x, const float* pa, const float* pb) {
+int tiled_cg_flush(Ctx& c, float* x, const float* pa, const float* pb,
+                   const unsigned char* grid_mask) {
   TiledArgs a{};
   a.g = c.g;
+  a.grid_mask = grid_mask;
   a.x = x;
   a.p = const_cast<float*>(pa);
   a.pb = const_cast<float*>(pb);

@@ -191,7 +191,8 @@ int tiled_cg_iterate(Ctx& c, const float* U32, float* r, float* x, float* pa, fl
                      float* Ap, double tol2, double delta2, int maxit, int n);
 // Before a reliable update of the fused tiled form: x += alpha_x p for the
 // chains about to be updated (their pending update of the iterate).
-int tiled_cg_flush(Ctx& c, float* x, const float* pa, const float* pb);
+int tiled_cg_flush(Ctx& c, float* x, const float* pa, const float* pb,
+                   const unsigned char* grid_mask);
 
 // Kernel times of deferred solves and their site-iterations (solver.cu);
 // call after the stream has been synchronised.

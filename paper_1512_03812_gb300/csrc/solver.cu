@@ -334,6 +334,7 @@ __global__ void k_cg_reset_masked(CgChain* cgc, const unsigned char* mask, int n
   if (c < n && !mask[c]) {
     cgc[c].state = 0;
     cgc[c].need_update = 0;
+    cgc[c].alpha_x = 0.0;
   }
 }
 
@@ -356,7 +357,7 @@ static int iterate(Ctx& c, CgArgs<R>& a, int n) {
 static int residual(Ctx& c, CgArgs<float>& a, double* xhi, const float* x, int all) {
   if (!all && x && tiled_cg_applies(c.L) && c.L->stream_ok) {
     // the fused tiled iteration leaves x += alpha p pending: apply it first
-    const int rc = tiled_cg_flush(c, a.x, a.pa, a.pb);
+    const int rc = tiled_cg_flush(c, a.x, a.pa, a.pb, a.grid_mask);
     if (rc) return rc;
   }
   k_cg_res_d<<<c.grid(), kBlock, 0, c.s>>>(c.g, a, xhi, x, all);

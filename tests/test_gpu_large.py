@@ -173,3 +173,27 @@ def test_bench_workload_sampled_chains(torch):
         assert abs(dH[c] - r.dH) < 1e-6 * max(1.0, abs(r.dH)), (c, dH[c], r.dH)
         if abs(u[c] - np.exp(-r.dH)) > 1e-4:
             assert bool(acc[c]) == r.accepted
+
+
+def test_hybrid_batch_fused_iteration(torch):
+    """A batch mixing chains the chain-resident kernels hold (60 x 60) with
+    one that only the grid-wide form can take (600 x 500): the small chains
+    are solved on a side stream while the large one takes the fused
+    streaming iteration (every chain is wide enough for the strips); all
+    reach the FP64 true residual, also through a second solve on the same
+    workspace."""
+    import paper_1512_03812_gb300 as P
+    shapes = [(60, 60), (600, 500), (60, 60)]
+    b = Batch(shapes, [2.0, 2.0, 1.5], [0.24, 0.25, 0.23], seed=97)
+    assert b.lat.N >= 1 << 18
+    q, psi = b.q(), b.spinor()
+    U64, U32 = b.lat.links(b.dev(q))
+    for k in range(2):
+        rhs = b.dev(psi if k == 0 else b.spinor(salt=9))
+        x, iters, relres = b.lat.cg_solve(U64, U32, rhs, P.CG(tol=1e-10, prec="mixed",
+                                                               delta=1e-3))
+        assert (relres <= 1e-10).all(), relres
+        r = rhs - b.lat.apply_DdagD(U64, x)
+        for c in range(len(shapes)):
+            assert np.linalg.norm(b.chain(r, c)) <= 1.0000001e-10 * np.linalg.norm(b.chain(rhs, c))
+    assert b.lat.check() == 0
