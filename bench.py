@@ -53,15 +53,24 @@ CG_BYTES_PER_SITE_ITER = {"mixed": (3 + 2) * 16 + (5 + 2) * 16, "f64": (3 + 2) *
 # R reads r, A p and writes r.
 FUSED_CG_BYTES_PER_SITE_ITER = (3 + 2) * 16 + 2 * 16 + (2 + 1) * 16
 # Shared-memory bytes per site and iteration of the chain-resident FP32 CG
-# (cg_chain.cu), by kernel variant.  Strided layout (0): p update 2 x 16,
-# t = D p reads 5 p + 3 U and writes t (9 x 16), D^dag t reads 5 t + 3 U + p
-# (9 x 16).  Column layouts (1 to 4, and the 4-block cluster of 128 x 128
-# chains): the t-neighbours, their link U_t(n - t) and the site's own value
-# come from registers, so D p reads p at x +- 1, p at t + 1, U and U(n - x)
-# and writes t (6 x 16), D^dag t the same on t plus p (6 x 16).
+# (cg_chain.cu), by kernel variant, in the steady state of a walk (the reads
+# that start each thread's strip are left out).  Strided layout (0): p update
+# 2 x 16, t = D p reads 5 p + 3 U and writes t (9 x 16), D^dag t reads 5 t +
+# 3 U + p (9 x 16).  Column layout (1, 2): the t-neighbour below, its link and
+# the site's own value come from registers, the links are split into x and t
+# halves and x += alpha p rides on the p update, so D p reads p at x +- 1 and
+# t + 1 (3 x 16), U_x, U_t (16) and U_x(n - x) (8) and writes t (16), D^dag t
+# the same without the write.  Two-block clusters (3, 4) and the 4-block
+# cluster of 128 x 128 chains: the column layout with whole-site links and the
+# p read of x += alpha p in the D^dag stage (2 x 6 x 16).  Column pairs (5, 6):
+# per two sites of a row, D reads 4 spinors (64) and 5 link halves (40) and
+# writes 2 (32); D^dag the same without the writes.
 SMEM_BYTES_STRIDED = 20 * 16
-SMEM_BYTES_COLUMN = 14 * 16
-SMEM_BYTES_BY_VARIANT = [SMEM_BYTES_STRIDED] + [SMEM_BYTES_COLUMN] * 4
+SMEM_BYTES_COLUMN = 2 * 16 + (4 * 16 + 8 + 16) + (3 * 16 + 8 + 16)
+SMEM_BYTES_CLUSTER = 14 * 16
+SMEM_BYTES_PAIR = 2 * 16 + (64 + 40 + 32) // 2 + (64 + 40) // 2
+SMEM_BYTES_BY_VARIANT = ([SMEM_BYTES_STRIDED] + [SMEM_BYTES_COLUMN] * 2 + [SMEM_BYTES_CLUSTER] * 2
+                         + [SMEM_BYTES_PAIR] * 2)
 # Shared-memory bandwidth per SM and clock (32 banks x 4 B).
 SMEM_BYTES_PER_CLK_PER_SM = 128
 NUM_SMS = 152
@@ -105,7 +114,8 @@ def ncu_traffic(kernel):
 
 # the chain-resident CG kernels by variant index (sm_set_cg_variant)
 CHAIN_KERNELS = ["k_cg_chain_mixed<8,512>", "k_cg_chain_col<8,512>", "k_cg_chain_col<16,256>",
-                 "k_cg_chain_cluster<8,256,2>", "k_cg_chain_cluster<4,512,2>"]
+                 "k_cg_chain_cluster<8,256,2>", "k_cg_chain_cluster<4,512,2>",
+                 "k_cg_chain_pair<4,512,64,64>", "k_cg_chain_pair<8,256,64,64>"]
 
 
 def kappa_to_m0(k):
@@ -283,7 +293,8 @@ def run_ours(args):
         v, vms = lat.autotune_cg(U64s, U32s, b_t, cgp)
         tune = {"variant": v, "ms_per_variant": [round(t, 3) for t in vms],
                 "variants": ["strided 512x8", "column 512x8", "column 256x16",
-                             "column 2-block cluster 256x8", "column 2-block cluster 512x4"]}
+                             "column 2-block cluster 256x8", "column 2-block cluster 512x4",
+                             "column pairs 512x2x4", "column pairs 256x2x8"]}
         log(f"autotuned chain CG: variant {v}, ms {vms}")
         del U64s, U32s, b_t
 
@@ -631,14 +642,14 @@ def run_other(args):
         # small chains take the strided kernel (320 B), the 128 x 128 ones the
         # 4-block cluster in the column layout (224 B): the lower figure is
         # used for all, so `achieved` is a lower bound
-        sach = SMEM_BYTES_COLUMN * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
+        sach = SMEM_BYTES_CLUSTER * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
         roofline = dict({"bound": "smem",
                          "kernel": "chain-resident CG (one block per small chain, 4-block "
                                    "clusters for 128x128 chains)",
                          "achieved": round(sach, 1), "peak": round(rates["smem_read_gbs"], 1),
                          "unit": "GB/s", "frac": round(sach / rates["smem_read_gbs"], 4),
                          "peak_source": "measured in this run (sm_peak_smem_read)",
-                         "bytes_per_site_iter": SMEM_BYTES_COLUMN,
+                         "bytes_per_site_iter": SMEM_BYTES_CLUSTER,
                          "hbm_equivalent": {"achieved": round(ach, 1), "peak": hbm,
                                             "frac": round(ach / hbm, 4),
                                             "bytes_per_site_iter": bps, "peak_source": src}},

@@ -37,6 +37,7 @@ SCHEMES = {
     "eleven_stage": 7,
 }
 FG_EXACT, FG_SHIFTED = 0, 1
+CG_VARIANTS = 7  # kernel variants of the chain-resident mixed CG (SM_CG_VARIANTS)
 PARTS = {"gauge": PART_GAUGE, "fermion": PART_FERMION, "full": PART_FULL}
 LAMBDA_2MN = 0.1931833275037836
 
@@ -287,7 +288,7 @@ class Lattice:
         (variant, [ms per variant or -1])."""
         x = torch.empty_like(b)
         v = ctypes.c_int()
-        ms = np.zeros(5)
+        ms = np.zeros(CG_VARIANTS)
         p = cg.c()
         _check(_LIB.sm_autotune_cg(self._h, _ptr(U64), _ptr(U32), _ptr(b), _ptr(x),
                                    ctypes.byref(p), *self._ws(), ctypes.byref(v), ms.ctypes.data,

@@ -358,10 +358,13 @@ struct ColWalk {
 // Column layout for chains whose shape matches the block: thread tid owns
 // column x = tid % L and the R consecutive rows t0 .. t0 + R - 1 of row block
 // tid / L.  D and D^dag walk down the column with a sliding window, so the
-// t-neighbours and U_t(n - t) come from registers and only the x-neighbours
-// and the links of the site are read from shared memory.  Every warp
-// finishes the block sums itself (FP32, the same order in every warp), so
-// all threads hold identical scalars and an iteration needs three barriers.
+// t-neighbours and the backward t-hop come from registers and only the
+// x-neighbours and the links are read from shared memory.  The links are held
+// as separate x and t halves, so U_x(n - x) is an 8-byte read, and the
+// iterate update x += alpha p waits for the next p update, which reads p
+// anyway (the reliable update applies it first).  Every warp finishes the
+// block sums itself (FP32, the same order in every warp), so all threads hold
+// identical scalars and an iteration needs three barriers.
 template <int R, int NT>
 __global__ void __launch_bounds__(NT, 1) k_cg_chain_col(ChainCgArgs a) {
   extern __shared__ float4 smem[];
@@ -370,14 +373,16 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_col(ChainCgArgs a) {
   const int c = a.list[blockIdx.x];
   const ChainInfo ci = a.chains[c];
   const int L = ci.L, T = ci.T, V = L * T;
-  float4* Us = smem;
-  float4* ps = smem + V;
-  float4* ts = smem + 2 * V;
+  float4* ps = smem;
+  float4* ts = smem + V;
+  float2* uxs = reinterpret_cast<float2*>(smem + 2 * V);
+  float2* uts = uxs + V;
   const float diag = (float)(2.0 + ci.m0);
   const int x = threadIdx.x % L, t0 = (threadIdx.x / L) * R;
   const int xp = x + 1 == L ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   auto site = [&](int t) { return (t < 0 ? t + T : (t >= T ? t - T : t)) * L; };
+  auto cx = [](float2 v) { return Cx<float>{v.x, v.y}; };
 
   // sum of one FP32 value per thread, finished by every warp
   auto bsum = [&](float v, float* buf) {
@@ -396,7 +401,9 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_col(ChainCgArgs a) {
 #pragma unroll
   for (int j = 0; j < R; ++j) {
     const int l = x + (t0 + j) * L;
-    Us[l] = __ldg(reinterpret_cast<const float4*>(a.U32) + ci.off + l);
+    const float4 u = __ldg(reinterpret_cast<const float4*>(a.U32) + ci.off + l);
+    uxs[l] = make_float2(u.x, u.y);
+    uts[l] = make_float2(u.z, u.w);
     const Sp<double> bv = ld_sp(a.b, ci.off + l);
     bbl += norm2(bv);
     rv[j] = to_flt(bv);
@@ -405,41 +412,41 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_col(ChainCgArgs a) {
     st_sp(a.x, ci.off + l, Sp<double>{{0, 0}, {0, 0}});
   }
   const double bb = cta_sum(bbl, redd);
-  // scalars, identical in every thread
-  float rr = (float)bb, rr_prev = rr, rmax = rr, beta = 0.f;
+  // scalars, identical in every thread; alpha is the last step's, owed to x
+  float rr = (float)bb, rr_prev = rr, rmax = rr, beta = 0.f, alpha = 0.f;
   const float tol2bb = (float)(a.tol2 * bb), delta2 = (float)a.delta2;
   double rr_true = bb;
   int it = 0, flags = isfinite(bb) ? 0 : 2, updates = 0;
   bool run = bb > 0.0 && isfinite(bb);
 
   while (run) {
+    // p = r + beta p, and the previous step's x += alpha p
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const int l = x + (t0 + j) * L;
-      ps[l] = f4_of(rv[j] + beta * sp_of(ps[l]));
+      const Sp<float> po = sp_of(ps[l]);
+      xv[j] = xv[j] + alpha * po;
+      ps[l] = f4_of(rv[j] + beta * po);
     }
     __syncthreads();
     // t = D p down the column
     float pap = 0.f;
     {
-      int rb = site(t0 - 1);
-      Sp<float> pm = sp_of(ps[x + rb]), pc = sp_of(ps[x + t0 * L]);
-      float4 um = Us[x + rb];
+      const int rb = site(t0 - 1);
+      Cx<float> g = hop_tm<false, float>(cx(uts[x + rb]), sp_of(ps[x + rb]));
+      Sp<float> pc = sp_of(ps[x + t0 * L]);
 #pragma unroll
       for (int j = 0; j < R; ++j) {
         const int row = (t0 + j) * L, rn = site(t0 + j + 1);
         const Sp<float> pn = sp_of(ps[x + rn]);
-        const float4 u = Us[x + row];
-        const float4 uxm = Us[xm + row];
-        const Sp<float> o = hop_sum<false, float>(sp_of(ps[xp + row]), sp_of(ps[xm + row]), pn,
-                                                  pm, {u.x, u.y}, {uxm.x, uxm.y}, {u.z, u.w},
-                                                  {um.z, um.w});
+        const Cx<float> ux = cx(uxs[x + row]), ut = cx(uts[x + row]);
+        const Sp<float> o = hop_sum_tm<false, float>(sp_of(ps[xp + row]), sp_of(ps[xm + row]), pn,
+                                                     ux, cx(uxs[xm + row]), ut, g);
         const Sp<float> tv = diag * pc - 0.5f * o;
         ts[x + row] = f4_of(tv);
         pap += norm2(tv);
-        pm = pc;
+        g = hop_tm<false, float>(ut, pc);
         pc = pn;
-        um = u;
         asm volatile("" ::: "memory");  // keep the next row's loads after this row
       }
     }
@@ -448,29 +455,25 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_col(ChainCgArgs a) {
       flags |= 2;
       break;
     }
-    const float alpha = rr / papt;
-    // A p = D^dag t down the column; x += alpha p; r -= alpha A p
+    alpha = rr / papt;
+    // A p = D^dag t down the column; r -= alpha A p
     float rn2 = 0.f;
     {
-      int rb = site(t0 - 1);
-      Sp<float> tm = sp_of(ts[x + rb]), tc = sp_of(ts[x + t0 * L]);
-      float4 um = Us[x + rb];
+      const int rb = site(t0 - 1);
+      Cx<float> g = hop_tm<true, float>(cx(uts[x + rb]), sp_of(ts[x + rb]));
+      Sp<float> tc = sp_of(ts[x + t0 * L]);
 #pragma unroll
       for (int j = 0; j < R; ++j) {
         const int row = (t0 + j) * L, rn = site(t0 + j + 1);
         const Sp<float> tn = sp_of(ts[x + rn]);
-        const float4 u = Us[x + row];
-        const float4 uxm = Us[xm + row];
-        const Sp<float> o = hop_sum<true, float>(sp_of(ts[xp + row]), sp_of(ts[xm + row]), tn, tm,
-                                                 {u.x, u.y}, {uxm.x, uxm.y}, {u.z, u.w},
-                                                 {um.z, um.w});
+        const Cx<float> ux = cx(uxs[x + row]), ut = cx(uts[x + row]);
+        const Sp<float> o = hop_sum_tm<true, float>(sp_of(ts[xp + row]), sp_of(ts[xm + row]), tn,
+                                                    ux, cx(uxs[xm + row]), ut, g);
         const Sp<float> Ap = diag * tc - 0.5f * o;
-        xv[j] = xv[j] + alpha * sp_of(ps[x + row]);
         rv[j] = rv[j] - alpha * Ap;
         rn2 += norm2(rv[j]);
-        tm = tc;
+        g = hop_tm<true, float>(ut, tc);
         tc = tn;
-        um = u;
         asm volatile("" ::: "memory");
       }
     }
@@ -485,13 +488,15 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_col(ChainCgArgs a) {
     }
     rmax = fmaxf(rmax, rr);
     if (rr <= tol2bb || rr < delta2 * rmax || it >= a.maxit) {
-      // reliable update: x_hi += x, r = b - A x_hi in FP64
+      // reliable update: x_hi += x + alpha p, r = b - A x_hi in FP64
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        const long long n = ci.off + x + (t0 + j) * L;
-        st_sp(a.x, n, ld_sp_cg(a.x, n) + to_dbl(xv[j]));
+        const int l = x + (t0 + j) * L;
+        const long long n = ci.off + l;
+        st_sp(a.x, n, ld_sp_cg(a.x, n) + to_dbl(xv[j] + alpha * sp_of(ps[l])));
         xv[j] = {{0.f, 0.f}, {0.f, 0.f}};
       }
+      alpha = 0.f;
       __syncthreads();
       {
         const ColWalk cw{a.U64, ci.off, L, T, x, xp, xm, t0, 2.0 + ci.m0};
@@ -538,10 +543,235 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_col(ChainCgArgs a) {
       rr = (float)rr_true;
       rmax = rr;
     }
-    // no barrier here: the next p update writes only the thread's own sites
-    // of ps, and the next D stage's writes of ts follow that update's barrier;
-    // every read of ts and of neighbouring ps in this iteration precedes the
-    // barrier inside the |r|^2 sum above
+    // no barrier here: the next p update reads and writes only the thread's
+    // own sites of ps, and the next D stage's writes of ts follow that
+    // update's barrier; every read of ts and of neighbouring ps in this
+    // iteration precedes the barrier inside the |r|^2 sum above
+  }
+  if (threadIdx.x == 0) {
+    CgChain* cc = a.cgc + c;
+    cc->bb = bb;
+    cc->rr = rr;
+    cc->rr_true = rr_true;
+    cc->iters = it;
+    cc->flags = flags;
+    cc->state = 0;
+    cc->need_update = updates;
+  }
+}
+
+// Column-pair layout for L x T chains (compile-time shape, L * T = 2 R NT):
+// thread tid owns the two columns 2k and 2k + 1 (k = tid % (L/2)) of the R
+// rows t0 .. t0 + R - 1 (t0 = (tid / (L/2)) R).  With the shape fixed, every
+// shared-memory address of a walk is a per-thread base plus a constant.  Shared memory stores every row with its even
+// columns first and its odd columns after them, so the x-neighbour between a
+// thread's two sites is its own and the two outer ones are the adjacent
+// threads' sites at consecutive addresses (no bank conflicts).  The links are
+// held as separate x and t halves, so U_x(n - x) is an 8-byte read.  Per
+// site-iteration this reads and writes about 168 bytes of shared memory
+// against about 200 for the one-column layout.  The iterate update
+// x += alpha p waits for the next p update, which reads p anyway (the
+// reliable update applies it first).  (Keeping the FP32 iterate in global
+// memory instead, updated by vector reductions at L2 to free its registers,
+// made the solve 27 % slower.)
+template <int R, int NT, int L, int T>
+__global__ void __launch_bounds__(NT, 1) k_cg_chain_pair(ChainCgArgs a) {
+  static_assert(L % 2 == 0 && L * T == 2 * R * NT, "one thread per two columns of R rows");
+  constexpr int V = L * T, H = L / 2;
+  extern __shared__ float4 smem[];
+  __shared__ float red[2][NT / 32];
+  __shared__ double redd[33];
+  const int c = a.list[blockIdx.x];
+  const ChainInfo ci = a.chains[c];
+  float4* ps = smem;
+  float4* ts = smem + V;
+  float2* uxs = reinterpret_cast<float2*>(smem + 2 * V);
+  float2* uts = uxs + V;
+  const float diag = (float)(2.0 + ci.m0);
+  const int k = threadIdx.x % H, t0 = (threadIdx.x / H) * R;
+  // positions within a row: the even column 2k, the odd column 2k + 1, the
+  // odd column 2k - 1 (x - 1 of the even site), the even column 2k + 2 (x + 1
+  // of the odd site)
+  const int qe = k, qo = H + k, qm = H + (k == 0 ? H - 1 : k - 1), qp = k + 1 == H ? 0 : k + 1;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // the rows below and above the thread's strip
+  const int rb = (t0 == 0 ? T - 1 : t0 - 1) * L, ra = (t0 + R == T ? 0 : t0 + R) * L;
+
+  auto bsum = [&](float v, float* buf) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) buf[w] = v;
+    __syncthreads();
+    float s = lane < NT / 32 ? buf[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+  };
+
+  // [2 j] the even site of row t0 + j, [2 j + 1] the odd one
+  Sp<float> rv[2 * R], xv[2 * R];
+  double bbl = 0.0;
+#pragma unroll
+  for (int i = 0; i < 2 * R; ++i) {
+    const int row = (t0 + i / 2) * L, l = row + 2 * k + (i & 1), q = row + ((i & 1) ? qo : qe);
+    const float4 u = __ldg(reinterpret_cast<const float4*>(a.U32) + ci.off + l);
+    uxs[q] = make_float2(u.x, u.y);
+    uts[q] = make_float2(u.z, u.w);
+    const Sp<double> bv = ld_sp(a.b, ci.off + l);
+    bbl += norm2(bv);
+    rv[i] = to_flt(bv);
+    xv[i] = {{0.f, 0.f}, {0.f, 0.f}};
+    ps[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    st_sp(a.x, ci.off + l, Sp<double>{{0, 0}, {0, 0}});
+  }
+  const double bb = cta_sum(bbl, redd);
+  float rr = (float)bb, rr_prev = rr, rmax = rr, beta = 0.f, alpha = 0.f;
+  const float tol2bb = (float)(a.tol2 * bb), delta2 = (float)a.delta2;
+  double rr_true = bb;
+  int it = 0, flags = isfinite(bb) ? 0 : 2, updates = 0;
+  bool run = bb > 0.0 && isfinite(bb);
+
+  // (D or D^dag) f on the thread's two columns, walking down its rows; emit(j,
+  // even, odd) receives the two results of row t0 + j
+  auto walk = [&](const float4* f, auto dag, auto emit) {
+    constexpr bool DAG = decltype(dag)::value;
+    auto cx = [](float2 v) { return Cx<float>{v.x, v.y}; };
+    // the backward t-hops into row t0, then the rows' own hops
+    Cx<float> ge = hop_tm<DAG, float>(cx(uts[rb + qe]), sp_of(f[rb + qe]));
+    Cx<float> go = hop_tm<DAG, float>(cx(uts[rb + qo]), sp_of(f[rb + qo]));
+    Sp<float> fce = sp_of(f[t0 * L + qe]), fco = sp_of(f[t0 * L + qo]);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int row = (t0 + j) * L, rn = j + 1 < R ? row + L : ra;
+      const Sp<float> fne = sp_of(f[rn + qe]), fno = sp_of(f[rn + qo]);
+      const Cx<float> uxe = cx(uxs[row + qe]), ute = cx(uts[row + qe]);
+      const Cx<float> uxo = cx(uxs[row + qo]), uto = cx(uts[row + qo]);
+      const Sp<float> oe =
+          hop_sum_tm<DAG, float>(fco, sp_of(f[row + qm]), fne, uxe, cx(uxs[row + qm]), ute, ge);
+      const Sp<float> oo = hop_sum_tm<DAG, float>(sp_of(f[row + qp]), fce, fno, uxo, uxe, uto, go);
+      emit(j, diag * fce - 0.5f * oe, diag * fco - 0.5f * oo);
+      ge = hop_tm<DAG, float>(ute, fce);
+      go = hop_tm<DAG, float>(uto, fco);
+      fce = fne;
+      fco = fno;
+      asm volatile("" ::: "memory");  // keep the next row's loads after this row
+    }
+  };
+
+  while (run) {
+    // p = r + beta p, and the previous step's x += alpha p
+#pragma unroll
+    for (int i = 0; i < 2 * R; ++i) {
+      const int row = (t0 + i / 2) * L, q = row + ((i & 1) ? qo : qe);
+      const Sp<float> po = sp_of(ps[q]);
+      xv[i] = xv[i] + alpha * po;
+      ps[q] = f4_of(rv[i] + beta * po);
+    }
+    __syncthreads();
+    float pap = 0.f;
+    walk(ps, std::false_type{}, [&](int j, const Sp<float>& te, const Sp<float>& to) {
+      const int row = (t0 + j) * L;
+      ts[row + qe] = f4_of(te);
+      ts[row + qo] = f4_of(to);
+      pap += norm2(te) + norm2(to);
+    });
+    const float papt = bsum(pap, red[0]);  // its barrier also publishes ts
+    if (!(papt > 0.f) || !isfinite(papt)) {
+      flags |= 2;
+      break;
+    }
+    alpha = rr / papt;
+    float rn2 = 0.f;
+    walk(ts, std::true_type{}, [&](int j, const Sp<float>& ae, const Sp<float>& ao) {
+      rv[2 * j] = rv[2 * j] - alpha * ae;
+      rv[2 * j + 1] = rv[2 * j + 1] - alpha * ao;
+      rn2 += norm2(rv[2 * j]) + norm2(rv[2 * j + 1]);
+    });
+    const float rrn = bsum(rn2, red[1]);
+    rr_prev = rr;
+    rr = rrn;
+    beta = rr / rr_prev;
+    ++it;
+    if (!isfinite(rr)) {
+      flags |= 2;
+      break;
+    }
+    rmax = fmaxf(rmax, rr);
+    if (rr <= tol2bb || rr < delta2 * rmax || it >= a.maxit) {
+      // reliable update: x_hi += x + alpha p, r = b - A x_hi in FP64
+#pragma unroll
+      for (int i = 0; i < 2 * R; ++i) {
+        const int row = (t0 + i / 2) * L;
+        const long long n = ci.off + row + 2 * k + (i & 1);
+        const Sp<float> xs = xv[i] + alpha * sp_of(ps[row + ((i & 1) ? qo : qe)]);
+        st_sp(a.x, n, ld_sp_cg(a.x, n) + to_dbl(xs));
+        xv[i] = {{0.f, 0.f}, {0.f, 0.f}};
+      }
+      alpha = 0.f;
+      __syncthreads();
+      {
+        // the walk down column 2k + s
+        auto col = [&](int s) {
+          const int xs = 2 * k + s;
+          return ColWalk{a.U64, ci.off, L, T, xs, xs + 1 == L ? 0 : xs + 1, xs == 0 ? L - 1 : xs - 1,
+                         t0, 2.0 + ci.m0};
+        };
+        // t64 = D x_hi down both columns
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const ColWalk cw = col(s);
+          Sp<double> fm = ld_sp_cg(a.x, cw.row(t0 - 1) + cw.x), fc = ld_sp_cg(a.x, cw.row(t0) + cw.x);
+          Cx<double> utm = ld_lk(a.U64, cw.row(t0 - 1) + cw.x).t;
+#pragma unroll 1
+          for (int j = 0; j < R; ++j) {
+            const Sp<double> fn = ld_sp_cg(a.x, cw.row(t0 + j + 1) + cw.x);
+            st_sp(a.t64, cw.row(t0 + j) + cw.x, cw.site<false>(a.x, j, fm, fc, fn, utm));
+            fm = fc;
+            fc = fn;
+          }
+        }
+        __syncthreads();
+        // r = b - D^dag t64 and |r|^2 (FP64); r goes to registers (FP32)
+        // through the thread's own sites of ts, free until the next D stage
+        double v = 0.0;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const ColWalk cw = col(s);
+          Sp<double> fm = ld_sp_cg(a.t64, cw.row(t0 - 1) + cw.x), fc = ld_sp_cg(a.t64, cw.row(t0) + cw.x);
+          Cx<double> utm = ld_lk(a.U64, cw.row(t0 - 1) + cw.x).t;
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            const Sp<double> fn = ld_sp_cg(a.t64, cw.row(t0 + j + 1) + cw.x);
+            const Sp<double> r =
+                ld_sp(a.b, cw.row(t0 + j) + cw.x) - cw.site<true>(a.t64, j, fm, fc, fn, utm);
+            v += norm2(r);
+            ts[(t0 + j) * L + (s ? qo : qe)] = f4_of(to_flt(r));
+            fm = fc;
+            fc = fn;
+            asm volatile("" ::: "memory");  // one row's loads at a time (registers)
+          }
+        }
+        rr_true = cta_sum(v, redd);
+#pragma unroll
+        for (int i = 0; i < 2 * R; ++i) rv[i] = sp_of(ts[(t0 + i / 2) * L + ((i & 1) ? qo : qe)]);
+      }
+      ++updates;
+      if (!isfinite(rr_true)) {
+        flags |= 2;
+        break;
+      }
+      if (rr_true <= a.tol2 * bb) break;
+      if (it >= a.maxit) {
+        flags |= 1;
+        break;
+      }
+      beta = (float)(rr_true / (double)rr_prev);
+      rr = (float)rr_true;
+      rmax = rr;
+    }
+    // no barrier here (as in the one-column layout): the next p update
+    // touches only the thread's own sites of ps, and every neighbour read of
+    // ps and ts in this iteration precedes the barrier of the |r|^2 sum
   }
   if (threadIdx.x == 0) {
     CgChain* cc = a.cgc + c;
@@ -871,7 +1101,13 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_cg_chain_f64(ChainCgArgs a
 // chain's shape to match).
 bool chain_variant_applies(const sm_lattice* L, int v) {
   if (v == 0) return true;
-  if (v < 0 || v > 4) return false;
+  if (v < 0 || v > 6) return false;
+  if (v >= 5) {
+    // column pairs of 64 x 64 chains: 512 threads x 4 rows, 256 x 8
+    for (const ChainInfo& ci : L->chains)
+      if (ci.L != 64 || ci.T != 64) return false;
+    return true;
+  }
   // rows of the chain the column layout covers: 512 x 8, 256 x 16, and for
   // the cluster forms 256 x 8 and 512 x 4 per half
   const int nt = (v == 1 || v == 4) ? 512 : 256, rows = v == 2 ? 16 : (v == 4 ? 4 : 8),
@@ -940,6 +1176,12 @@ int chain_cg_prepare(const sm_lattice* L, const sm_cg_params& cg) {
     e = cudaFuncSetAttribute(k_cg_chain_col<8, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_cg_chain_col<16, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_chain_pair<4, 512, 64, 64>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_chain_pair<8, 256, 64, 64>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_cg_chain_mixed<1, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
@@ -1070,6 +1312,10 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
       go(k_cg_chain_col<8, 512>, 512);
     } else if (v == 2) {
       go(k_cg_chain_col<16, 256>, 256);
+    } else if (v == 5) {
+      go(k_cg_chain_pair<4, 512, 64, 64>, 512);
+    } else if (v == 6) {
+      go(k_cg_chain_pair<8, 256, 64, 64>, 256);
     } else if (vmax <= 1024) {
       // x and r of every site live in registers: 8 floats per site, so the
       // largest chains use 512 threads with 8 sites each (up to 128

@@ -228,6 +228,41 @@ __device__ __forceinline__ Sp<R> hop_sum(Sp<R> xp, Sp<R> xm, Sp<R> tp, Sp<R> tm,
   return o;
 }
 
+// *p += v in global memory without waiting for the result (a vector
+// reduction, performed at L2)
+__device__ __forceinline__ void red_add4s(float4* p, float4 v) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(p), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w)
+               : "memory");
+}
+
+// hop_sum split for walks down a column: hop_tm is the backward t-hop that
+// the site above n receives from n, conj(U_t(n)) (1 -/+ s2 projection of f(n)),
+// computed while n is the current row; hop_sum_tm adds the other three hops.
+template <bool DAG, typename R>
+__device__ __forceinline__ Cx<R> hop_tm(Cx<R> ut, Sp<R> f) {
+  return cmul_conj(ut, DAG ? f.a + mul_i(f.b) : f.a - mul_i(f.b));
+}
+template <bool DAG, typename R>
+__device__ __forceinline__ Sp<R> hop_sum_tm(Sp<R> xp, Sp<R> xm, Sp<R> tp, Cx<R> ux, Cx<R> uxm,
+                                            Cx<R> ut, Cx<R> h4) {
+  Sp<R> o;
+  if (!DAG) {
+    const Cx<R> h1 = ux * (xp.a - xp.b);
+    const Cx<R> h2 = cmul_conj(uxm, xm.a + xm.b);
+    const Cx<R> h3 = ut * (tp.a + mul_i(tp.b));
+    o.a = (h1 + h2) + (h3 + h4);
+    o.b = (h2 - h1) + (mul_i(h4) - mul_i(h3));
+  } else {
+    const Cx<R> h1 = ux * (xp.a + xp.b);
+    const Cx<R> h2 = cmul_conj(uxm, xm.a - xm.b);
+    const Cx<R> h3 = ut * (tp.a - mul_i(tp.b));
+    o.a = (h1 + h2) + (h3 + h4);
+    o.b = (h1 - h2) + (mul_i(h3) - mul_i(h4));
+  }
+  return o;
+}
+
 // The bilinears of the fermion force at link (n, mu):
 //   A = a(n)^dag (1 - s_mu) U_mu(n) b(n+mu),  B = a(n+mu)^dag (1 + s_mu) U_mu(n)^* b(n)
 // (Eq. force_fermion has f = -Im(A - B) with a = chi, b = xi).

@@ -171,7 +171,7 @@ int launch_ddagd(Ctx& c, const R* U, const R* in, R* out);
 bool chain_cg_fits(const sm_lattice* L, int prec);
 bool chain_variant_applies(const sm_lattice* L, int v);
 bool big_chain_shape(const ChainInfo& ci);
-constexpr int kChainVariants = 5;
+constexpr int kChainVariants = SM_CG_VARIANTS;
 int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
                     const sm_cg_params& cg);
 

@@ -45,14 +45,6 @@ struct CgFuse {
 };
 constexpr int kSRingCG = kSStages * 3 * kSW;  // float4 per warp in the CG form
 
-// *p += v in global memory without waiting for the result (a vector
-// reduction, performed at L2)
-__device__ __forceinline__ void red_add4s(float4* p, float4 v) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(p), "f"(v.x), "f"(v.y),
-               "f"(v.z), "f"(v.w)
-               : "memory");
-}
-
 // Ring slot of window site s: pairs of slots are swapped in every second
 // group of 8, so that a lane reading sites 2 l (or 2 l + 1) and the copies
 // writing sites l, l + 32 both touch 32 distinct banks per quarter-warp.

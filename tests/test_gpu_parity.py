@@ -152,12 +152,13 @@ def test_cg_layouts_agree(torch):
         assert rel_err(b.chain(xg, c), b.chain(xc, c)) < 1e-12
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 def test_chain_cg_kernel_variants_64x64(torch, variant):
     """Every kernel variant of the chain-resident mixed CG (strided, column
-    512x8, column 256x16, two-block cluster) on 64x64 chains: the FP64 true
-    residual meets the tolerance and x agrees with the FP64 solve; one
-    trajectory matches the oracle's Delta H and decision."""
+    512x8, column 256x16, two-block clusters, column pairs 512x4 and 256x8) on
+    64x64 chains: the FP64 true residual meets the
+    tolerance and x agrees with the FP64 solve; one trajectory matches the
+    oracle's Delta H and decision."""
     import paper_1512_03812_gb300 as P
     b = batch(torch, dims=[(64, 64)] * 3, betas=2.0, kappas=0.24, seed=9)
     b.lat.set_cg_variant(variant)
@@ -180,6 +181,23 @@ def test_chain_cg_kernel_variants_64x64(torch, variant):
                            "adapted_nested_fg", 0.25, 1, M=2, solver=sw.Solver(1e-13))
     assert abs(dH[0] - ro.dH) < 1e-6, (dH[0], ro.dH)
     assert bool(acc[0]) == ro.accepted
+
+
+def test_column_pair_variants_need_64x64_chains(torch):
+    """The column-pair kernels are compiled for 64 x 64 chains: pinning them
+    on other shapes (here 32 x 128, which the 512 x 8 column layout takes) is
+    an argument error, and the lattice keeps its variant."""
+    import paper_1512_03812_gb300 as P
+    b = batch(torch, dims=[(32, 128)] * 2, betas=2.0, kappas=0.24, seed=3)
+    b.lat.set_cg_variant(1)
+    for v in (5, 6):
+        with pytest.raises(P.SchwingerError):
+            b.lat.set_cg_variant(v)
+    q, phi = b.q(), b.spinor()
+    U64, U32 = b.lat.links(b.dev(q))
+    xm, iters, relres = b.lat.cg_solve(U64, U32, b.dev(phi),
+                                       P.CG(tol=1e-10, prec="mixed", delta=0.01, algo="chain"))
+    assert (relres <= 1e-10).all(), relres
 
 
 def test_mixed_batch_with_128x128_chains(torch):
