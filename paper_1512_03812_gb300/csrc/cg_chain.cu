@@ -207,6 +207,13 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_mixed(ChainCgArgs a) {
     }
   }
   const double bb = cta_sum(bbl, red);
+  if (bb == 0.0) {  // x = 0: D x, which the reliable updates otherwise leave in t64
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) {
+      const int l = threadIdx.x + k * blockDim.x;
+      if (l < V) st_sp(a.t64, ci.off + l, Sp<double>{{0, 0}, {0, 0}});
+    }
+  }
   if (threadIdx.x == 0) {
     S.bb = bb;
     S.rr = S.rr_prev = S.rmax = S.rr_true = bb;
@@ -412,6 +419,9 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_col(ChainCgArgs a) {
     st_sp(a.x, ci.off + l, Sp<double>{{0, 0}, {0, 0}});
   }
   const double bb = cta_sum(bbl, redd);
+  if (bb == 0.0)  // x = 0: D x, which the reliable updates otherwise leave in t64
+#pragma unroll
+    for (int j = 0; j < R; ++j) st_sp(a.t64, ci.off + x + (t0 + j) * L, Sp<double>{{0, 0}, {0, 0}});
   // scalars, identical in every thread; alpha is the last step's, owed to x
   float rr = (float)bb, rr_prev = rr, rmax = rr, beta = 0.f, alpha = 0.f;
   const float tol2bb = (float)(a.tol2 * bb), delta2 = (float)a.delta2;
@@ -563,17 +573,18 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_col(ChainCgArgs a) {
 // Column-pair layout for L x T chains (compile-time shape, L * T = 2 R NT):
 // thread tid owns the two columns 2k and 2k + 1 (k = tid % (L/2)) of the R
 // rows t0 .. t0 + R - 1 (t0 = (tid / (L/2)) R).  With the shape fixed, every
-// shared-memory address of a walk is a per-thread base plus a constant.  Shared memory stores every row with its even
-// columns first and its odd columns after them, so the x-neighbour between a
-// thread's two sites is its own and the two outer ones are the adjacent
-// threads' sites at consecutive addresses (no bank conflicts).  The links are
-// held as separate x and t halves, so U_x(n - x) is an 8-byte read.  Per
-// site-iteration this reads and writes about 168 bytes of shared memory
-// against about 200 for the one-column layout.  The iterate update
-// x += alpha p waits for the next p update, which reads p anyway (the
-// reliable update applies it first).  (Keeping the FP32 iterate in global
-// memory instead, updated by vector reductions at L2 to free its registers,
-// made the solve 27 % slower.)
+// shared-memory address of a walk is a per-thread base plus a constant.
+// Shared memory stores every row with its even columns first and its odd
+// columns after them, so the x-neighbour between a thread's two sites is its
+// own and the two outer ones are the adjacent threads' sites at consecutive
+// addresses (no bank conflicts).  The links are held as separate x and t
+// halves, so U_x(n - x) is an 8-byte read.  The iterate update x += alpha p
+// waits for the next p update, which reads p anyway (the reliable update
+// applies it first).  Per site-iteration the 256 x 8 form moves about 162
+// bytes of shared memory, the one-column layout about 202.  Two forms that
+// were slower: the FP32 iterate in global memory, updated by vector
+// reductions at L2 to free its registers (27 % slower), and the thread's own
+// p kept in registers besides shared memory (spills; 24 % slower).
 template <int R, int NT, int L, int T>
 __global__ void __launch_bounds__(NT, 1) k_cg_chain_pair(ChainCgArgs a) {
   static_assert(L % 2 == 0 && L * T == 2 * R * NT, "one thread per two columns of R rows");
@@ -625,6 +636,10 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_pair(ChainCgArgs a) {
     st_sp(a.x, ci.off + l, Sp<double>{{0, 0}, {0, 0}});
   }
   const double bb = cta_sum(bbl, redd);
+  if (bb == 0.0)  // x = 0: D x, which the reliable updates otherwise leave in t64
+#pragma unroll
+    for (int i = 0; i < 2 * R; ++i)
+      st_sp(a.t64, ci.off + (t0 + i / 2) * L + 2 * k + (i & 1), Sp<double>{{0, 0}, {0, 0}});
   float rr = (float)bb, rr_prev = rr, rmax = rr, beta = 0.f, alpha = 0.f;
   const float tol2bb = (float)(a.tol2 * bb), delta2 = (float)a.delta2;
   double rr_true = bb;
@@ -877,6 +892,9 @@ __global__ void __launch_bounds__(NT, (K == 2 && NT == 256 ? 2 : 1)) k_cg_chain_
     st_sp(a.x, base + l, Sp<double>{{0, 0}, {0, 0}});
   }
   const double bb = csumd(bbl);
+  if (bb == 0.0)  // x = 0: D x, which the reliable updates otherwise leave in t64
+#pragma unroll
+    for (int j = 0; j < R; ++j) st_sp(a.t64, base + x + (t0 + j) * L, Sp<double>{{0, 0}, {0, 0}});
   float rr = (float)bb, rr_prev = rr, rmax = rr, beta = 0.f;
   const float tol2bb = (float)(a.tol2 * bb), delta2 = (float)a.delta2;
   double rr_true = bb;
@@ -1216,7 +1234,7 @@ int chain_cg_accumulate(Ctx& c) {
 // The chains of a mixed batch that fit the shared-memory form, solved by the
 // strided kernel (one block each) on c.s; the other chains are untouched.
 int chain_cg_launch_list(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
-                         const sm_cg_params& cg) {
+                         const sm_cg_params& cg, double* dx) {
   const sm_lattice* L = c.L;
   ChainCgArgs a{};
   a.chains = L->d_chains;
@@ -1225,7 +1243,7 @@ int chain_cg_launch_list(Ctx& c, const double* U64, const float* U32, const doub
   a.U64 = U64;
   a.b = b;
   a.x = x;
-  a.t64 = c.w.t;
+  a.t64 = dx ? dx : c.w.t;
   a.r64 = c.w.r;
   a.p64 = c.w.p0;
   a.cgc = c.w.cgc;
@@ -1253,7 +1271,7 @@ int chain_cg_launch_list(Ctx& c, const double* U64, const float* U32, const doub
 }
 
 int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
-                    const sm_cg_params& cg) {
+                    const sm_cg_params& cg, double* dx) {
   const sm_lattice* L = c.L;
   ChainCgArgs a{};
   a.chains = L->d_chains;
@@ -1262,7 +1280,7 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
   a.U64 = U64;
   a.b = b;
   a.x = x;
-  a.t64 = c.w.t;
+  a.t64 = dx ? dx : c.w.t;
   a.r64 = c.w.r;
   a.p64 = c.w.p0;
   a.cgc = c.w.cgc;
@@ -1280,7 +1298,7 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
     if (L->nbig < L->nchains) {
       Ctx cs = c;
       cs.s = L->side;
-      if ((rc = chain_cg_launch_list(cs, U64, U32, b, x, cg))) return rc;
+      if ((rc = chain_cg_launch_list(cs, U64, U32, b, x, cg, dx))) return rc;
     }
     ChainCgArgs ab = a;
     ab.list = L->d_big_list;

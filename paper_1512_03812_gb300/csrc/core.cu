@@ -325,10 +325,12 @@ __global__ void __launch_bounds__(kBlock) k_deriv_hop(Geo g, const double* __res
 //   C(n,mu) = 4 Re[ Z1^dag w_{2,n,mu} + w_{1,n,mu}^dag Z2 - chi^dag d2D xi v(n,mu) ]
 // which in terms of the link bilinears A(a,b), B(a,b) of the fermion force is
 //   C = 2 Im[A(Z1,xi) - B(Z1,xi) + A(chi,Z2) - B(chi,Z2)] - 2 v Re[A(chi,xi) + B(chi,xi)].
+// Z1 is z1 - z1s when z1s is not NULL (z1 = D Z2 from the solver, z1s = s2).
 __global__ void __launch_bounds__(kBlock) k_fg_assemble(Geo g, const double* __restrict__ U,
                                                         const double* __restrict__ chi,
                                                         const double* __restrict__ xi,
                                                         const double* __restrict__ z1,
+                                                        const double* __restrict__ z1s,
                                                         const double* __restrict__ z2,
                                                         const double* __restrict__ v,
                                                         double* __restrict__ C, int acc) {
@@ -337,13 +339,14 @@ __global__ void __launch_bounds__(kBlock) k_fg_assemble(Geo g, const double* __r
   const long long nb[2] = {at(s, xp1(s), s.t), at(s, s.x, tp1(s))};
   const Lk<double> u = ld_lk(U, s.n);
   const Sp<double> c0 = ld_sp(chi, s.n), x0 = ld_sp(xi, s.n);
-  const Sp<double> a0 = ld_sp(z1, s.n), b0 = ld_sp(z2, s.n);
+  auto ldz1 = [&](long long n) { return z1s ? ld_sp(z1, n) - ld_sp(z1s, n) : ld_sp(z1, n); };
+  const Sp<double> a0 = ldz1(s.n), b0 = ld_sp(z2, s.n);
   const double2 vn = ld_l2(v, s.n);
   double out[2];
 #pragma unroll
   for (int mu = 0; mu < 2; ++mu) {
     const Sp<double> c1 = ld_sp(chi, nb[mu]), x1 = ld_sp(xi, nb[mu]);
-    const Sp<double> a1 = ld_sp(z1, nb[mu]), b1 = ld_sp(z2, nb[mu]);
+    const Sp<double> a1 = ldz1(nb[mu]), b1 = ld_sp(z2, nb[mu]);
     Cx<double> A0, B0, A1, B1, A2, B2;
     if (mu == 0) {
       bilinear_x(c0, c1, x0, x1, u.x, A0, B0);
@@ -498,8 +501,9 @@ int launch_deriv_hop(Ctx& c, const double* U64, const double* v, const double* i
   return launched(c.st, "deriv_hop");
 }
 int launch_fg_assemble(Ctx& c, const double* U64, const double* chi, const double* xi,
-                       const double* z1, const double* z2, const double* v, double* C, bool acc) {
-  k_fg_assemble<<<c.grid(), kBlock, 0, c.s>>>(c.g, U64, chi, xi, z1, z2, v, C, acc ? 1 : 0);
+                       const double* z1, const double* z1s, const double* z2, const double* v,
+                       double* C, bool acc) {
+  k_fg_assemble<<<c.grid(), kBlock, 0, c.s>>>(c.g, U64, chi, xi, z1, z1s, z2, v, C, acc ? 1 : 0);
   return launched(c.st, "fg_assemble");
 }
 int launch_gauge_hvp(Ctx& c, const double* q, const double* v, double* C, bool acc) {

@@ -142,8 +142,10 @@ int launch_fermion_kick(Ctx& c, const double* U64, const double* chi, const doub
                         double eps, double* Fout, bool acc);
 int launch_deriv_hop(Ctx& c, const double* U64, const double* v, const double* in, double* out,
                      bool dagger);
+// Z1 = z1 - z1s (z1s may be NULL: Z1 = z1).
 int launch_fg_assemble(Ctx& c, const double* U64, const double* chi, const double* xi,
-                       const double* z1, const double* z2, const double* v, double* C, bool acc);
+                       const double* z1, const double* z1s, const double* z2, const double* v,
+                       double* C, bool acc);
 int launch_gauge_hvp(Ctx& c, const double* q, const double* v, double* C, bool acc);
 int launch_axpy_links(Ctx& c, double* y, const double* x, double a, const double* z, double b);
 int launch_drift(Ctx& c, double* q, const double* p, double eps);
@@ -172,8 +174,11 @@ bool chain_cg_fits(const sm_lattice* L, int prec);
 bool chain_variant_applies(const sm_lattice* L, int v);
 bool big_chain_shape(const ChainInfo& ci);
 constexpr int kChainVariants = SM_CG_VARIANTS;
+// SM_MIXED kernels leave D x of the result in dx (FP64 [N][2][2]; the last
+// FP64 reliable update computes it; zero where b = 0) when dx is not NULL,
+// else use the workspace's scratch for it.
 int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
-                    const sm_cg_params& cg);
+                    const sm_cg_params& cg, double* dx = nullptr);
 
 // Sets the launch attributes of the chain-resident kernel a solve with
 // these parameters will use (done before a CUDA-graph capture).
@@ -182,7 +187,7 @@ int chain_cg_prepare(const sm_lattice* L, const sm_cg_params& cg);
 bool chain_cg_selected(const sm_lattice* L, const sm_cg_params& cg);
 int chain_cg_accumulate(Ctx& c);
 int chain_cg_launch_list(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
-                         const sm_cg_params& cg);
+                         const sm_cg_params& cg, double* dx = nullptr);
 
 // The tiled grid-wide mixed iteration (cg_tiled.cu) for batches of 2^18
 // sites or more: n iterations of P, AP, XR on r, x, p (in place), Ap.
@@ -199,8 +204,13 @@ int tiled_cg_flush(Ctx& c, float* x, const float* pa, const float* pb,
 int profile_collect_deferred(const sm_lattice* L, const int* chain_iters);
 
 // CG on D^dag D (solver.cu).  b, x FP64; x is overwritten.  If iters/relres
-// are non-NULL they receive host copies.  Synchronises.
+// are non-NULL they receive host copies.  Synchronises (except in deferred
+// mode).  If dx is not NULL, solves that compute D x of the result in FP64
+// anyway (the chain-resident mixed ones, in their last reliable update) leave
+// it there and set *have_dx; otherwise *have_dx is false and dx is untouched
+// or scratch.
 int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
-             const sm_cg_params& cg, int* iters, double* relres);
+             const sm_cg_params& cg, int* iters, double* relres, double* dx = nullptr,
+             bool* have_dx = nullptr);
 
 }  // namespace sm

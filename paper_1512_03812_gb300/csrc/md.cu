@@ -42,12 +42,14 @@ static int make_links(Ctx& c, const double* q, double* U64, float* U32, const sm
 }
 
 // xi = (D^dag D)^{-1} phi and chi = D xi (Eq. chi_xi_vectors), in c.w.xi, c.w.chi.
+// chi comes from the solver where its last FP64 reliable update computed it.
 static int chi_xi(Ctx& c, const double* U64, const float* U32, const double* phi,
                   const sm_cg_params& cg) {
-  SM_TRY(cg_solve(c, U64, U32, phi, c.w.xi, cg, nullptr, nullptr));
+  bool have = false;
+  SM_TRY(cg_solve(c, U64, U32, phi, c.w.xi, cg, nullptr, nullptr, c.w.chi, &have));
   c.st->inversions += 2;
   c.st->force_evals++;
-  return launch_dslash<double>(c, U64, c.w.xi, c.w.chi, false, nullptr, 0.0);
+  return have ? SM_OK : launch_dslash<double>(c, U64, c.w.xi, c.w.chi, false, nullptr, 0.0);
 }
 
 // The force of `part` at q (links U64/U32 of q): written to F (if not NULL)
@@ -77,10 +79,13 @@ static int hess_times(Ctx& c, const double* q, const double* U64, const float* U
     SM_TRY(launch_deriv_hop(c, U64, v, c.w.chi, c.w.s1, true));   // sum w_1 v
     SM_TRY(launch_deriv_hop(c, U64, v, c.w.xi, c.w.s2, false));   // sum w_2 v
     SM_TRY(launch_dslash<double>(c, U64, c.w.s2, c.w.b, true, c.w.s1, 1.0));
-    SM_TRY(cg_solve(c, U64, U32, c.w.b, c.w.z2, cg, nullptr, nullptr));
+    // Z1 = D Z2 - s2: D Z2 from the solver where it computed it
+    bool have = false;
+    SM_TRY(cg_solve(c, U64, U32, c.w.b, c.w.z2, cg, nullptr, nullptr, c.w.z1, &have));
     c.st->inversions += 2;
-    SM_TRY(launch_dslash<double>(c, U64, c.w.z2, c.w.z1, false, c.w.s2, -1.0));
-    SM_TRY(launch_fg_assemble(c, U64, c.w.chi, c.w.xi, c.w.z1, c.w.z2, v, C, acc));
+    if (!have) SM_TRY(launch_dslash<double>(c, U64, c.w.z2, c.w.z1, false, c.w.s2, -1.0));
+    SM_TRY(launch_fg_assemble(c, U64, c.w.chi, c.w.xi, c.w.z1, have ? c.w.s2 : nullptr, c.w.z2,
+                              v, C, acc));
   }
   return SM_OK;
 }

@@ -409,7 +409,8 @@ static int run(Ctx& c, CgArgs<R>& a, CgArgs<float>& af, int chunk, int maxit, lo
 }
 
 int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
-             const sm_cg_params& cg, int* iters, double* relres) {
+             const sm_cg_params& cg, int* iters, double* relres, double* dx, bool* have_dx) {
+  if (have_dx) *have_dx = false;
   if (!U64 || !b || !x) return fail(SM_ERR_ARG, "cg_solve: NULL field");
   if (!(cg.tol > 0.0) || cg.maxit < 1) return fail(SM_ERR_ARG, "cg_solve: bad tol or maxit");
   const bool mixed = cg.prec == SM_MIXED;
@@ -446,6 +447,8 @@ int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, doubl
   // A batch of both kinds (AUTO, mixed): the chains that fit are solved
   // chain-resident on the side stream while the others iterate grid-wide.
   const bool hybrid = !chain && cg.algo == SM_CG_AUTO && mixed && c.L->nsmall > 0 && !c.deferred;
+  // the chain-resident mixed kernels compute D x of the result
+  double* dxk = chain && mixed ? dx : nullptr;
 
   SM_CU(cudaMemsetAsync(c.w.n_active, 0, sizeof(int), c.s));
   long long batched = 0, updates = 0;
@@ -455,14 +458,16 @@ int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, doubl
     // no readback: the chain's flags and iterations accumulate on the device
     const bool timed = g_prof.on && !c.capturing && g_prof.nd < Profile::kPool;
     if (timed) SM_CU(cudaEventRecord(g_prof.d0[g_prof.nd], c.s));
-    if ((rc = chain_cg_launch(c, U64, U32, b, x, cg))) return rc;
+    if ((rc = chain_cg_launch(c, U64, U32, b, x, cg, dxk))) return rc;
     if (timed) SM_CU(cudaEventRecord(g_prof.d1[g_prof.nd++], c.s));
     c.st->cg_solves++;
+    if (have_dx) *have_dx = dxk != nullptr;
     return chain_cg_accumulate(c);
   }
   if (chain) {
     if ((rc = prof_record(g_prof.e0, 0, c.s))) return rc;
-    if ((rc = chain_cg_launch(c, U64, U32, b, x, cg))) return rc;
+    if ((rc = chain_cg_launch(c, U64, U32, b, x, cg, dxk))) return rc;
+    if (have_dx) *have_dx = dxk != nullptr;
     if ((rc = prof_record(g_prof.e1, 0, c.s))) return rc;
     SM_CU(cudaStreamSynchronize(c.s));
     if ((rc = prof_collect(0, false))) return rc;

@@ -181,6 +181,17 @@ def test_chain_cg_kernel_variants_64x64(torch, variant):
                            "adapted_nested_fg", 0.25, 1, M=2, solver=sw.Solver(1e-13))
     assert abs(dH[0] - ro.dH) < 1e-6, (dH[0], ro.dH)
     assert bool(acc[0]) == ro.accepted
+    # the fermion force takes chi = D xi from the kernel's last reliable
+    # update; a chain with a zero pseudofermion gets zero force
+    eta0 = eta.copy()
+    eta0[b.off[2]:b.off[3]] = 0.0
+    qd = b.dev(q)
+    phi0 = b.lat.apply_D(U64, b.dev(eta0), dagger=True)
+    Fm = b.lat.fermion_force(qd, phi0, P.CG(tol=1e-13, prec="mixed", delta=0.01, algo="chain"))
+    F64 = b.lat.fermion_force(qd, phi0, cg(1e-14))
+    for c in range(2):
+        assert rel_err(b.chain(Fm, c), b.chain(F64, c)) < 1e-10
+    assert np.abs(b.chain(Fm, 2)).max() == 0.0
 
 
 def test_column_pair_variants_need_64x64_chains(torch):
@@ -271,6 +282,37 @@ def test_force_gradient(torch, part):
         Fo, Co = sw.force_and_gradient(ol, U, ph, sw.Solver(1e-14), part)
         assert rel_err(b.chain(F, c), Fo) < TOL64
         assert rel_err(b.chain(C, c), Co) < 1e-11
+
+
+@pytest.mark.parametrize("algo", ["chain", "grid"])
+def test_mixed_fermion_force_and_gradient(torch, algo):
+    """With mixed-precision solves the chain-resident kernels hand back D x of
+    the solution from their last FP64 reliable update, which the fermion force
+    (chi = D xi) and the force gradient (Z1 = D Z2 - s2) use; grid-wide solves
+    apply D instead.  Both agree with the oracle, and a chain whose
+    pseudofermion is zero (x = 0 without an update) gets zero fermion force
+    and gradient."""
+    import paper_1512_03812_gb300 as P
+    b = batch(torch)
+    q, eta = b.q(), b.eta()
+    eta[b.off[1]:b.off[2]] = 0.0
+    qd = b.dev(q)
+    U64, _ = b.lat.links(qd)
+    phi = b.lat.apply_D(U64, b.dev(eta), dagger=True)
+    cgm = P.CG(tol=1e-13, prec="mixed", delta=0.01, algo=algo)
+    Ff = b.lat.fermion_force(qd, phi, cgm)
+    F = b.lat.field()
+    C = b.lat.force_gradient(qd, phi, "fermion", cgm, F=F)
+    for c, ol in enumerate(b.olat):
+        U = sw.links(b.chain(q, c))
+        ph = sw.apply_D(ol, U, b.chain(eta, c), dagger=True)
+        Fo, Co = sw.force_and_gradient(ol, U, ph, sw.Solver(1e-14), "fermion")
+        if c == 1:
+            assert np.abs(b.chain(Ff, c)).max() == 0.0 and np.abs(b.chain(C, c)).max() == 0.0
+            continue
+        assert rel_err(b.chain(Ff, c), Fo) < 1e-10
+        assert rel_err(b.chain(F, c), Fo) < 1e-10
+        assert rel_err(b.chain(C, c), Co) < 1e-9
 
 
 @pytest.mark.parametrize("part", ["gauge", "fermion", "full"])
