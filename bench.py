@@ -62,7 +62,7 @@ FUSED_CG_BYTES_PER_SITE_ITER = (3 + 2) * 16 + 2 * 16 + (2 + 1) * 16
 # t + 1 (3 x 16), U_x, U_t (16) and U_x(n - x) (8) and writes t (16), D^dag t
 # the same without the write.  Two-block clusters (3, 4) and the 4-block
 # cluster of 128 x 128 chains: the column layout with whole-site links and the
-# p read of x += alpha p in the D^dag stage (2 x 6 x 16).  Column pairs (5, 6):
+# p read of x += alpha p in the D^dag stage (2 x 6 x 16).  Column pairs (5-7):
 # per two sites of a row, D reads 4 spinors (64) and 5 link halves (40) and
 # writes 2 (32); D^dag the same without the writes.
 SMEM_BYTES_STRIDED = 20 * 16
@@ -70,7 +70,7 @@ SMEM_BYTES_COLUMN = 2 * 16 + (4 * 16 + 8 + 16) + (3 * 16 + 8 + 16)
 SMEM_BYTES_CLUSTER = 14 * 16
 SMEM_BYTES_PAIR = 2 * 16 + (64 + 40 + 32) // 2 + (64 + 40) // 2
 SMEM_BYTES_BY_VARIANT = ([SMEM_BYTES_STRIDED] + [SMEM_BYTES_COLUMN] * 2 + [SMEM_BYTES_CLUSTER] * 2
-                         + [SMEM_BYTES_PAIR] * 2)
+                         + [SMEM_BYTES_PAIR] * 3)
 # Shared-memory bandwidth per SM and clock (32 banks x 4 B).
 SMEM_BYTES_PER_CLK_PER_SM = 128
 NUM_SMS = 152
@@ -78,7 +78,7 @@ NUM_SMS = 152
 # the committed ncu captures, keyed by kernel, with the sources they were
 # taken on: a changed source makes the figure stale (reported as null)
 NCU_CAPTURES = {
-    "k_cg_chain_pair<8,256,64,64>": {
+    "k_cg_chain_pair<8,256,64,64,1>": {
         "sources": {"paper_1512_03812_gb300/csrc/cg_chain.cu": "0c93590fb4b790fb",
                     "paper_1512_03812_gb300/csrc/common.cuh": "636a9beaa370d51d"},
         "dram_bytes_per_launch": 118445312 + 60159744},
@@ -116,7 +116,8 @@ def ncu_traffic(kernel):
 # the chain-resident CG kernels by variant index (sm_set_cg_variant)
 CHAIN_KERNELS = ["k_cg_chain_mixed<8,512>", "k_cg_chain_col<8,512>", "k_cg_chain_col<16,256>",
                  "k_cg_chain_cluster<8,256,2>", "k_cg_chain_cluster<4,512,2>",
-                 "k_cg_chain_pair<4,512,64,64>", "k_cg_chain_pair<8,256,64,64>"]
+                 "k_cg_chain_pair<4,512,64,64,1>", "k_cg_chain_pair<8,256,64,64,1>",
+                 "k_cg_chain_pair<8,128,64,64,2>"]
 
 
 def kappa_to_m0(k):
@@ -295,7 +296,8 @@ def run_ours(args):
         tune = {"variant": v, "ms_per_variant": [round(t, 3) for t in vms],
                 "variants": ["strided 512x8", "column 512x8", "column 256x16",
                              "column 2-block cluster 256x8", "column 2-block cluster 512x4",
-                             "column pairs 512x2x4", "column pairs 256x2x8"]}
+                             "column pairs 512x2x4", "column pairs 256x2x8",
+                             "column pairs 2-block cluster 128x2x8"]}
         log(f"autotuned chain CG: variant {v}, ms {vms}")
         del U64s, U32s, b_t
 

@@ -37,7 +37,7 @@ SCHEMES = {
     "eleven_stage": 7,
 }
 FG_EXACT, FG_SHIFTED = 0, 1
-CG_VARIANTS = 7  # kernel variants of the chain-resident mixed CG (SM_CG_VARIANTS)
+CG_VARIANTS = 8  # kernel variants of the chain-resident mixed CG (SM_CG_VARIANTS)
 PARTS = {"gauge": PART_GAUGE, "fermion": PART_FERMION, "full": PART_FULL}
 LAMBDA_2MN = 0.1931833275037836
 

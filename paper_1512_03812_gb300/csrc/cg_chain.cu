@@ -570,52 +570,118 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_col(ChainCgArgs a) {
   }
 }
 
-// Column-pair layout for L x T chains (compile-time shape, L * T = 2 R NT):
+// Cluster helpers for kernels compiled with and without clusters (K = 1:
+// the block alone).
+template <int K>
+__device__ __forceinline__ void ksync() {
+  if constexpr (K > 1)
+    cooperative_groups::this_cluster().sync();
+  else
+    __syncthreads();
+}
+template <int K, typename P>
+__device__ __forceinline__ P* kmap(P* p, unsigned r) {
+  if constexpr (K > 1)
+    return cooperative_groups::this_cluster().map_shared_rank(p, r);
+  else
+    return p;
+}
+template <int K>
+__device__ __forceinline__ unsigned krank() {
+  if constexpr (K > 1)
+    return cooperative_groups::this_cluster().block_rank();
+  else
+    return 0;
+}
+
+// Column-pair layout for L x T chains (compile-time shape, L * T = 2 R NT K):
 // thread tid owns the two columns 2k and 2k + 1 (k = tid % (L/2)) of the R
-// rows t0 .. t0 + R - 1 (t0 = (tid / (L/2)) R).  With the shape fixed, every
-// shared-memory address of a walk is a per-thread base plus a constant.
-// Shared memory stores every row with its even columns first and its odd
-// columns after them, so the x-neighbour between a thread's two sites is its
-// own and the two outer ones are the adjacent threads' sites at consecutive
-// addresses (no bank conflicts).  The links are held as separate x and t
-// halves, so U_x(n - x) is an 8-byte read.  The iterate update x += alpha p
-// waits for the next p update, which reads p anyway (the reliable update
-// applies it first).  Per site-iteration the 256 x 8 form moves about 162
-// bytes of shared memory, the one-column layout about 202.  Two forms that
-// were slower: the FP32 iterate in global memory, updated by vector
-// reductions at L2 to free its registers (27 % slower), and the thread's own
-// p kept in registers besides shared memory (spills; 24 % slower).
-template <int R, int NT, int L, int T>
-__global__ void __launch_bounds__(NT, 1) k_cg_chain_pair(ChainCgArgs a) {
-  static_assert(L % 2 == 0 && L * T == 2 * R * NT, "one thread per two columns of R rows");
-  constexpr int V = L * T, H = L / 2;
+// rows t0 .. t0 + R - 1 (t0 = (tid / (L/2)) R) of its block's part of the
+// chain.  With K > 1 the chain is split over a cluster of K blocks, block
+// rank r holding the rows [r T/K, (r+1) T/K); the row below a block's part
+// and the row above come from ranks r - 1 and r + 1 (distributed shared
+// memory, wrapping with the lattice), and block sums are added across the
+// cluster in rank order, so every block takes the same decisions and passes
+// the same cluster barriers.  With the shape fixed, every shared-memory
+// address of a walk is a per-thread base plus a constant.  Shared memory
+// stores every row with its even columns first and its odd columns after
+// them, so the x-neighbour between a thread's two sites is its own and the
+// two outer ones are the adjacent threads' sites at consecutive addresses (no
+// bank conflicts).  The links are held as separate x and t halves, so
+// U_x(n - x) is an 8-byte read.  The iterate update x += alpha p waits for
+// the next p update, which reads p anyway (the reliable update applies it
+// first).  Per site-iteration the 256 x 8 form moves about 162 bytes of
+// shared memory, the one-column layout about 202.  Two forms that were
+// slower: the FP32 iterate in global memory, updated by vector reductions at
+// L2 to free its registers (27 % slower), and the thread's own p kept in
+// registers besides shared memory (spills; 24 % slower).
+template <int R, int NT, int L, int T, int K>
+__global__ void __launch_bounds__(NT, K == 2 ? 2 : 1) k_cg_chain_pair(ChainCgArgs a) {
+  static_assert(L % 2 == 0 && T % K == 0 && L * T == 2 * R * NT * K,
+                "one thread per two columns of R rows");
+  constexpr int H = T / K, V = H * L, HL = L / 2;  // rows and sites of a block's part
   extern __shared__ float4 smem[];
   __shared__ float red[2][NT / 32];
   __shared__ double redd[33];
-  const int c = a.list[blockIdx.x];
+  __shared__ float slot[2];  // this block's part of the two sums of an iteration
+  __shared__ double slotd;   // this block's part of an FP64 sum
+  const unsigned rank = krank<K>();
+  const int c = a.list[blockIdx.x / K];
   const ChainInfo ci = a.chains[c];
+  const long long base = ci.off + (long long)rank * V;  // first global site of the part
   float4* ps = smem;
   float4* ts = smem + V;
   float2* uxs = reinterpret_cast<float2*>(smem + 2 * V);
   float2* uts = uxs + V;
+  // the parts below and above (this block's own with K = 1)
+  const unsigned rkb = (rank + K - 1) % K, rka = (rank + 1) % K;
+  const float4* psb = kmap<K>(ps, rkb);
+  const float4* psa = kmap<K>(ps, rka);
+  const float4* tsb = kmap<K>(ts, rkb);
+  const float4* tsa = kmap<K>(ts, rka);
+  const float2* utsb = kmap<K>(uts, rkb);
   const float diag = (float)(2.0 + ci.m0);
-  const int k = threadIdx.x % H, t0 = (threadIdx.x / H) * R;
+  const int k = threadIdx.x % HL, t0 = (threadIdx.x / HL) * R;
   // positions within a row: the even column 2k, the odd column 2k + 1, the
   // odd column 2k - 1 (x - 1 of the even site), the even column 2k + 2 (x + 1
   // of the odd site)
-  const int qe = k, qo = H + k, qm = H + (k == 0 ? H - 1 : k - 1), qp = k + 1 == H ? 0 : k + 1;
+  const int qe = k, qo = HL + k, qm = HL + (k == 0 ? HL - 1 : k - 1), qp = k + 1 == HL ? 0 : k + 1;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  // the rows below and above the thread's strip
-  const int rb = (t0 == 0 ? T - 1 : t0 - 1) * L, ra = (t0 + R == T ? 0 : t0 + R) * L;
+  // the rows below and above the thread's strip: offsets in the part that
+  // holds them, which is the one below (above) for the strip at the bottom
+  // (top) of the part
+  const bool bot = t0 == 0, top = t0 + R == H;
+  const int rb = bot ? (H - 1) * L : (t0 - 1) * L, ra = top ? 0 : (t0 + R) * L;
 
-  auto bsum = [&](float v, float* buf) {
+  // sum of one FP32 value per thread over the chain, the same in every thread
+  auto tsum = [&](float v, int kk) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) buf[w] = v;
+    if (lane == 0) red[kk][w] = v;
     __syncthreads();
-    float s = lane < NT / 32 ? buf[lane] : 0.f;
+    float s = lane < NT / 32 ? red[kk][lane] : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if constexpr (K > 1) {
+      if (threadIdx.x == 0) slot[kk] = s;
+      ksync<K>();
+      s = 0.f;
+#pragma unroll
+      for (int j = 0; j < K; ++j) s += kmap<K>(slot, j)[kk];
+    }
+    return s;
+  };
+  // FP64 sum over the chain
+  auto tsumd = [&](double v) {
+    double s = cta_sum(v, redd);
+    if constexpr (K > 1) {
+      if (threadIdx.x == 0) slotd = s;
+      ksync<K>();
+      s = 0.0;
+#pragma unroll
+      for (int j = 0; j < K; ++j) s += *kmap<K>(&slotd, j);
+      ksync<K>();  // all have read before slotd is written again
+    }
     return s;
   };
 
@@ -625,40 +691,45 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_pair(ChainCgArgs a) {
 #pragma unroll
   for (int i = 0; i < 2 * R; ++i) {
     const int row = (t0 + i / 2) * L, l = row + 2 * k + (i & 1), q = row + ((i & 1) ? qo : qe);
-    const float4 u = __ldg(reinterpret_cast<const float4*>(a.U32) + ci.off + l);
+    const float4 u = __ldg(reinterpret_cast<const float4*>(a.U32) + base + l);
     uxs[q] = make_float2(u.x, u.y);
     uts[q] = make_float2(u.z, u.w);
-    const Sp<double> bv = ld_sp(a.b, ci.off + l);
+    const Sp<double> bv = ld_sp(a.b, base + l);
     bbl += norm2(bv);
     rv[i] = to_flt(bv);
     xv[i] = {{0.f, 0.f}, {0.f, 0.f}};
     ps[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    st_sp(a.x, ci.off + l, Sp<double>{{0, 0}, {0, 0}});
+    st_sp(a.x, base + l, Sp<double>{{0, 0}, {0, 0}});
   }
-  const double bb = cta_sum(bbl, redd);
+  const double bb = tsumd(bbl);
   if (bb == 0.0)  // x = 0: D x, which the reliable updates otherwise leave in t64
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i)
-      st_sp(a.t64, ci.off + (t0 + i / 2) * L + 2 * k + (i & 1), Sp<double>{{0, 0}, {0, 0}});
+      st_sp(a.t64, base + (t0 + i / 2) * L + 2 * k + (i & 1), Sp<double>{{0, 0}, {0, 0}});
   float rr = (float)bb, rr_prev = rr, rmax = rr, beta = 0.f, alpha = 0.f;
   const float tol2bb = (float)(a.tol2 * bb), delta2 = (float)a.delta2;
   double rr_true = bb;
   int it = 0, flags = isfinite(bb) ? 0 : 2, updates = 0;
   bool run = bb > 0.0 && isfinite(bb);
 
-  // (D or D^dag) f on the thread's two columns, walking down its rows; emit(j,
-  // even, odd) receives the two results of row t0 + j
-  auto walk = [&](const float4* f, auto dag, auto emit) {
+  // (D or D^dag) f on the thread's two columns, walking down its rows (fb,
+  // fa: f of the parts below and above); emit(j, even, odd) receives the two
+  // results of row t0 + j
+  auto walk = [&](const float4* f, const float4* fb, const float4* fa, auto dag, auto emit) {
     constexpr bool DAG = decltype(dag)::value;
     auto cx = [](float2 v) { return Cx<float>{v.x, v.y}; };
+    const float4* fbr = (bot ? fb : f) + rb;
+    const float2* ubr = (bot ? utsb : uts) + rb;
+    const float4* far = (top ? fa : f) + ra;
     // the backward t-hops into row t0, then the rows' own hops
-    Cx<float> ge = hop_tm<DAG, float>(cx(uts[rb + qe]), sp_of(f[rb + qe]));
-    Cx<float> go = hop_tm<DAG, float>(cx(uts[rb + qo]), sp_of(f[rb + qo]));
+    Cx<float> ge = hop_tm<DAG, float>(cx(ubr[qe]), sp_of(fbr[qe]));
+    Cx<float> go = hop_tm<DAG, float>(cx(ubr[qo]), sp_of(fbr[qo]));
     Sp<float> fce = sp_of(f[t0 * L + qe]), fco = sp_of(f[t0 * L + qo]);
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-      const int row = (t0 + j) * L, rn = j + 1 < R ? row + L : ra;
-      const Sp<float> fne = sp_of(f[rn + qe]), fno = sp_of(f[rn + qo]);
+      const int row = (t0 + j) * L;
+      const float4* fn = j + 1 < R ? f + row + L : far;
+      const Sp<float> fne = sp_of(fn[qe]), fno = sp_of(fn[qo]);
       const Cx<float> uxe = cx(uxs[row + qe]), ute = cx(uts[row + qe]);
       const Cx<float> uxo = cx(uxs[row + qo]), uto = cx(uts[row + qo]);
       const Sp<float> oe =
@@ -682,27 +753,27 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_pair(ChainCgArgs a) {
       xv[i] = xv[i] + alpha * po;
       ps[q] = f4_of(rv[i] + beta * po);
     }
-    __syncthreads();
+    ksync<K>();  // every part's p (and, the first time, U) is written
     float pap = 0.f;
-    walk(ps, std::false_type{}, [&](int j, const Sp<float>& te, const Sp<float>& to) {
+    walk(ps, psb, psa, std::false_type{}, [&](int j, const Sp<float>& te, const Sp<float>& to) {
       const int row = (t0 + j) * L;
       ts[row + qe] = f4_of(te);
       ts[row + qo] = f4_of(to);
       pap += norm2(te) + norm2(to);
     });
-    const float papt = bsum(pap, red[0]);  // its barrier also publishes ts
+    const float papt = tsum(pap, 0);  // its barrier also publishes ts
     if (!(papt > 0.f) || !isfinite(papt)) {
       flags |= 2;
       break;
     }
     alpha = rr / papt;
     float rn2 = 0.f;
-    walk(ts, std::true_type{}, [&](int j, const Sp<float>& ae, const Sp<float>& ao) {
+    walk(ts, tsb, tsa, std::true_type{}, [&](int j, const Sp<float>& ae, const Sp<float>& ao) {
       rv[2 * j] = rv[2 * j] - alpha * ae;
       rv[2 * j + 1] = rv[2 * j + 1] - alpha * ao;
       rn2 += norm2(rv[2 * j]) + norm2(rv[2 * j + 1]);
     });
-    const float rrn = bsum(rn2, red[1]);
+    const float rrn = tsum(rn2, 1);
     rr_prev = rr;
     rr = rrn;
     beta = rr / rr_prev;
@@ -717,48 +788,49 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_pair(ChainCgArgs a) {
 #pragma unroll
       for (int i = 0; i < 2 * R; ++i) {
         const int row = (t0 + i / 2) * L;
-        const long long n = ci.off + row + 2 * k + (i & 1);
+        const long long n = base + row + 2 * k + (i & 1);
         const Sp<float> xs = xv[i] + alpha * sp_of(ps[row + ((i & 1) ? qo : qe)]);
         st_sp(a.x, n, ld_sp_cg(a.x, n) + to_dbl(xs));
         xv[i] = {{0.f, 0.f}, {0.f, 0.f}};
       }
       alpha = 0.f;
-      __syncthreads();
+      ksync<K>();
       {
-        // the walk down column 2k + s
+        // the walk down column 2k + s from the strip's first row in the chain
+        const int tg = (int)rank * H + t0;
         auto col = [&](int s) {
           const int xs = 2 * k + s;
           return ColWalk{a.U64, ci.off, L, T, xs, xs + 1 == L ? 0 : xs + 1, xs == 0 ? L - 1 : xs - 1,
-                         t0, 2.0 + ci.m0};
+                         tg, 2.0 + ci.m0};
         };
         // t64 = D x_hi down both columns
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
           const ColWalk cw = col(s);
-          Sp<double> fm = ld_sp_cg(a.x, cw.row(t0 - 1) + cw.x), fc = ld_sp_cg(a.x, cw.row(t0) + cw.x);
-          Cx<double> utm = ld_lk(a.U64, cw.row(t0 - 1) + cw.x).t;
+          Sp<double> fm = ld_sp_cg(a.x, cw.row(tg - 1) + cw.x), fc = ld_sp_cg(a.x, cw.row(tg) + cw.x);
+          Cx<double> utm = ld_lk(a.U64, cw.row(tg - 1) + cw.x).t;
 #pragma unroll 1
           for (int j = 0; j < R; ++j) {
-            const Sp<double> fn = ld_sp_cg(a.x, cw.row(t0 + j + 1) + cw.x);
-            st_sp(a.t64, cw.row(t0 + j) + cw.x, cw.site<false>(a.x, j, fm, fc, fn, utm));
+            const Sp<double> fn = ld_sp_cg(a.x, cw.row(tg + j + 1) + cw.x);
+            st_sp(a.t64, cw.row(tg + j) + cw.x, cw.site<false>(a.x, j, fm, fc, fn, utm));
             fm = fc;
             fc = fn;
           }
         }
-        __syncthreads();
+        ksync<K>();
         // r = b - D^dag t64 and |r|^2 (FP64); r goes to registers (FP32)
         // through the thread's own sites of ts, free until the next D stage
         double v = 0.0;
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
           const ColWalk cw = col(s);
-          Sp<double> fm = ld_sp_cg(a.t64, cw.row(t0 - 1) + cw.x), fc = ld_sp_cg(a.t64, cw.row(t0) + cw.x);
-          Cx<double> utm = ld_lk(a.U64, cw.row(t0 - 1) + cw.x).t;
+          Sp<double> fm = ld_sp_cg(a.t64, cw.row(tg - 1) + cw.x), fc = ld_sp_cg(a.t64, cw.row(tg) + cw.x);
+          Cx<double> utm = ld_lk(a.U64, cw.row(tg - 1) + cw.x).t;
 #pragma unroll
           for (int j = 0; j < R; ++j) {
-            const Sp<double> fn = ld_sp_cg(a.t64, cw.row(t0 + j + 1) + cw.x);
+            const Sp<double> fn = ld_sp_cg(a.t64, cw.row(tg + j + 1) + cw.x);
             const Sp<double> r =
-                ld_sp(a.b, cw.row(t0 + j) + cw.x) - cw.site<true>(a.t64, j, fm, fc, fn, utm);
+                ld_sp(a.b, cw.row(tg + j) + cw.x) - cw.site<true>(a.t64, j, fm, fc, fn, utm);
             v += norm2(r);
             ts[(t0 + j) * L + (s ? qo : qe)] = f4_of(to_flt(r));
             fm = fc;
@@ -766,7 +838,7 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_pair(ChainCgArgs a) {
             asm volatile("" ::: "memory");  // one row's loads at a time (registers)
           }
         }
-        rr_true = cta_sum(v, redd);
+        rr_true = tsumd(v);
 #pragma unroll
         for (int i = 0; i < 2 * R; ++i) rv[i] = sp_of(ts[(t0 + i / 2) * L + ((i & 1) ? qo : qe)]);
       }
@@ -788,7 +860,8 @@ __global__ void __launch_bounds__(NT, 1) k_cg_chain_pair(ChainCgArgs a) {
     // touches only the thread's own sites of ps, and every neighbour read of
     // ps and ts in this iteration precedes the barrier of the |r|^2 sum
   }
-  if (threadIdx.x == 0) {
+  if constexpr (K > 1) ksync<K>();  // no block leaves while another may read its shared memory
+  if (threadIdx.x == 0 && rank == 0) {
     CgChain* cc = a.cgc + c;
     cc->bb = bb;
     cc->rr = rr;
@@ -1119,9 +1192,10 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_cg_chain_f64(ChainCgArgs a
 // chain's shape to match).
 bool chain_variant_applies(const sm_lattice* L, int v) {
   if (v == 0) return true;
-  if (v < 0 || v > 6) return false;
+  if (v < 0 || v > 7) return false;
   if (v >= 5) {
-    // column pairs of 64 x 64 chains: 512 threads x 4 rows, 256 x 8
+    // column pairs of 64 x 64 chains: 512 threads x 4 rows, 256 x 8, and
+    // 2-block clusters of 128 x 8
     for (const ChainInfo& ci : L->chains)
       if (ci.L != 64 || ci.T != 64) return false;
     return true;
@@ -1195,11 +1269,17 @@ int chain_cg_prepare(const sm_lattice* L, const sm_cg_params& cg) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_cg_chain_col<16, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_cg_chain_pair<4, 512, 64, 64>,
+    e = cudaFuncSetAttribute(k_cg_chain_pair<4, 512, 64, 64, 1>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_cg_chain_pair<8, 256, 64, 64>,
+    e = cudaFuncSetAttribute(k_cg_chain_pair<8, 256, 64, 64, 1>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_chain_pair<8, 128, 64, 64, 2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem / 2);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_chain_pair<8, 256, 128, 128, 4>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 4096 * 16);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_cg_chain_mixed<1, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
@@ -1302,8 +1382,15 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
     }
     ChainCgArgs ab = a;
     ab.list = L->d_big_list;
-    e = launch_cluster<4>(k_cg_chain_cluster<8, 512, 4>, L->nbig, 512, (size_t)3 * 4096 * 16,
-                          c.s, ab);
+    bool sq128 = true;  // all large chains 128 x 128: the column-pair form
+    for (const ChainInfo& ci : L->chains)
+      if (ci.L * ci.T > kChainMaxVolume) sq128 = sq128 && ci.L == 128 && ci.T == 128;
+    if (sq128)
+      e = launch_cluster<4>(k_cg_chain_pair<8, 256, 128, 128, 4>, L->nbig, 256,
+                            (size_t)3 * 4096 * 16, c.s, ab);
+    else
+      e = launch_cluster<4>(k_cg_chain_cluster<8, 512, 4>, L->nbig, 512, (size_t)3 * 4096 * 16,
+                            c.s, ab);
     if (e != cudaSuccess) return fail(SM_ERR_CUDA, "chain CG (clusters): %s", cudaGetErrorString(e));
     if ((rc = launched(c.st, "cg_chain_cluster4"))) return rc;
     e = cudaEventRecord(L->ev_join, L->side);
@@ -1331,9 +1418,11 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
     } else if (v == 2) {
       go(k_cg_chain_col<16, 256>, 256);
     } else if (v == 5) {
-      go(k_cg_chain_pair<4, 512, 64, 64>, 512);
+      go(k_cg_chain_pair<4, 512, 64, 64, 1>, 512);
     } else if (v == 6) {
-      go(k_cg_chain_pair<8, 256, 64, 64>, 256);
+      go(k_cg_chain_pair<8, 256, 64, 64, 1>, 256);
+    } else if (v == 7) {
+      e = launch_cluster<2>(k_cg_chain_pair<8, 128, 64, 64, 2>, L->nchains, 128, smem / 2, c.s, a);
     } else if (vmax <= 1024) {
       // x and r of every site live in registers: 8 floats per site, so the
       // largest chains use 512 threads with 8 sites each (up to 128

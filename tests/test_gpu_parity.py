@@ -152,11 +152,11 @@ def test_cg_layouts_agree(torch):
         assert rel_err(b.chain(xg, c), b.chain(xc, c)) < 1e-12
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
 def test_chain_cg_kernel_variants_64x64(torch, variant):
     """Every kernel variant of the chain-resident mixed CG (strided, column
-    512x8, column 256x16, two-block clusters, column pairs 512x4 and 256x8) on
-    64x64 chains: the FP64 true residual meets the
+    512x8, column 256x16, two-block clusters, column pairs 512x4, 256x8 and in
+    two-block clusters) on 64x64 chains: the FP64 true residual meets the
     tolerance and x agrees with the FP64 solve; one trajectory matches the
     oracle's Delta H and decision."""
     import paper_1512_03812_gb300 as P
@@ -201,7 +201,7 @@ def test_column_pair_variants_need_64x64_chains(torch):
     import paper_1512_03812_gb300 as P
     b = batch(torch, dims=[(32, 128)] * 2, betas=2.0, kappas=0.24, seed=3)
     b.lat.set_cg_variant(1)
-    for v in (5, 6):
+    for v in (5, 6, 7):
         with pytest.raises(P.SchwingerError):
             b.lat.set_cg_variant(v)
     q, phi = b.q(), b.spinor()
@@ -237,6 +237,24 @@ def test_mixed_batch_with_128x128_chains(torch):
                            "adapted_nested_fg", 0.2, 1, M=2, solver=sw.Solver(1e-13))
     assert abs(dH[0] - ro.dH) < 1e-6, (dH[0], ro.dH)
     assert b.lat.check() == 0
+
+
+def test_large_chains_of_other_shapes(torch):
+    """Large chains that are not all 128 x 128 (here 64 x 256 beside one) take
+    the one-column 4-block cluster kernel; 128 x 128 ones alone the
+    column-pair cluster kernel.  Both meet the tolerance and agree with the
+    FP64 solve."""
+    import paper_1512_03812_gb300 as P
+    for dims in ([(64, 256), (128, 128), (32, 32)], [(128, 128), (128, 128)]):
+        b = batch(torch, dims=dims, betas=(2.0, 1.0, 3.0), kappas=(0.24, 0.22, 0.23), seed=5)
+        q, phi = b.q(), b.spinor()
+        U64, U32 = b.lat.links(b.dev(q))
+        x64, _, _ = b.lat.cg_solve(U64, U32, b.dev(phi), cg(1e-12))
+        xm, iters, relres = b.lat.cg_solve(U64, U32, b.dev(phi),
+                                           P.CG(tol=1e-10, prec="mixed", delta=0.01, algo="chain"))
+        assert (relres <= 1e-10).all(), relres
+        for c in range(len(dims)):
+            assert rel_err(b.chain(xm, c), b.chain(x64, c)) < 1e-8
 
 
 def test_chain_solver_rejects_oversized_chains(torch):
