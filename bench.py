@@ -645,16 +645,16 @@ def run_other(args):
         # memory, so the bound is shared-memory bandwidth (HBM-equivalent
         # bytes beside it for context)
         # small chains take the strided kernel (320 B), the 128 x 128 ones the
-        # 4-block cluster in the column layout (224 B): the lower figure is
-        # used for all, so `achieved` is a lower bound
-        sach = SMEM_BYTES_CLUSTER * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
+        # 4-block column-pair cluster (152 B): the lower figure is used for
+        # all, so `achieved` is a lower bound
+        sach = SMEM_BYTES_PAIR * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
         roofline = dict({"bound": "smem",
                          "kernel": "chain-resident CG (one block per small chain, 4-block "
-                                   "clusters for 128x128 chains)",
+                                   "column-pair clusters for 128x128 chains)",
                          "achieved": round(sach, 1), "peak": round(rates["smem_read_gbs"], 1),
                          "unit": "GB/s", "frac": round(sach / rates["smem_read_gbs"], 4),
                          "peak_source": "measured in this run (sm_peak_smem_read)",
-                         "bytes_per_site_iter": SMEM_BYTES_CLUSTER,
+                         "bytes_per_site_iter": SMEM_BYTES_PAIR,
                          "hbm_equivalent": {"achieved": round(ach, 1), "peak": hbm,
                                             "frac": round(ach / hbm, 4),
                                             "bytes_per_site_iter": bps, "peak_source": src}},
