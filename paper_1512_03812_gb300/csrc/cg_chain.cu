@@ -728,8 +728,14 @@ __global__ void __launch_bounds__(NT, K == 2 ? 2 : 1) k_cg_chain_pair(ChainCgArg
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const int row = (t0 + j) * L;
-      const float4* fn = j + 1 < R ? f + row + L : far;
-      const Sp<float> fne = sp_of(fn[qe]), fno = sp_of(fn[qo]);
+      Sp<float> fne, fno;  // the row above: the thread's next row, or the strip's row above
+      if (j + 1 < R) {      // (an index, not a pointer select: fewer registers)
+        fne = sp_of(f[row + L + qe]);
+        fno = sp_of(f[row + L + qo]);
+      } else {
+        fne = sp_of(far[qe]);
+        fno = sp_of(far[qo]);
+      }
       const Cx<float> uxe = cx(uxs[row + qe]), ute = cx(uts[row + qe]);
       const Cx<float> uxo = cx(uxs[row + qo]), uto = cx(uts[row + qo]);
       const Sp<float> oe =
