@@ -38,7 +38,7 @@ struct TiledArgs {
   CgChain* cgc;
   double* partials;
   unsigned* counters;
-  int* n_active;
+  int* n_active;  // [0] chains still iterating, [1] chains due a reliable update
   int* err;
   const unsigned char* grid_mask;  // hybrid solves: 0 for chains solved chain-resident
   double tol2, delta2;
@@ -270,25 +270,29 @@ __global__ void __launch_bounds__(kSThreads) k_cgt_r(TiledArgs a) {
       atomicSub(a.n_active, 1);
     } else if (rr <= a.tol2 * cc->bb || cc->iters >= a.maxit) {
       cc->state = 2;  // wait for the FP64 check
-      cc->need_update = 1;
+      mark_update(cc, a.n_active + 1);
     } else if (rr < a.delta2 * cc->rmax) {
-      cc->need_update = 1;
+      mark_update(cc, a.n_active + 1);
     }
     cc->rmax = fmax(cc->rmax, rr);
   }
 }
 
-// x += alpha_x p for the chains about to take a reliable update
+// x += alpha_x p for the chains about to take a reliable update (a block
+// visits the site blocks blockIdx.x, + gridDim.x, ...)
 __global__ void __launch_bounds__(kBlock) k_cgt_xflush(TiledArgs a) {
-  const int c = a.g.blk_chain[blockIdx.x];
-  if (a.grid_mask && !a.grid_mask[c]) return;
-  const CgChain* cc = a.cgc + c;
-  if (!cc->need_update || cc->alpha_x == 0.0) return;
-  const ChainInfo ci = a.g.chains[c];
-  const Site s = site_of(a.g, ci, c);
-  if (!s.valid) return;
-  const float* p = cc->par ? a.pb : a.p;
-  st_sp(a.x, s.n, ld_sp_cg(a.x, s.n) + (float)cc->alpha_x * ld_sp_cg(p, s.n));
+  if (a.n_active[1] == 0) return;  // no chain is due an update
+  for (int blk = blockIdx.x; blk < a.g.nblocks; blk += gridDim.x) {
+    const int c = a.g.blk_chain[blk];
+    if (a.grid_mask && !a.grid_mask[c]) continue;
+    const CgChain* cc = a.cgc + c;
+    if (!cc->need_update || cc->alpha_x == 0.0) continue;
+    const ChainInfo ci = a.g.chains[c];
+    const Site s = site_of(a.g, ci, c, blk);
+    if (!s.valid) continue;
+    const float* p = cc->par ? a.pb : a.p;
+    st_sp(a.x, s.n, ld_sp_cg(a.x, s.n) + (float)cc->alpha_x * ld_sp_cg(p, s.n));
+  }
 }
 
 int cgt_fused_occupancy() {
@@ -331,9 +335,9 @@ __global__ void __launch_bounds__(kBlock) k_cgt_xr(TiledArgs a) {
       atomicSub(a.n_active, 1);
     } else if (rr <= a.tol2 * cc->bb || cc->iters >= a.maxit) {
       cc->state = 2;  // wait for the FP64 check
-      cc->need_update = 1;
+      mark_update(cc, a.n_active + 1);
     } else if (rr < a.delta2 * cc->rmax) {
-      cc->need_update = 1;
+      mark_update(cc, a.n_active + 1);
     }
     cc->rmax = fmax(cc->rmax, rr);
   }
@@ -350,7 +354,8 @@ int tiled_cg_flush(Ctx& c, float* x, const float* pa, const float* pb,
   a.p = const_cast<float*>(pa);
   a.pb = const_cast<float*>(pb);
   a.cgc = c.w.cgc;
-  k_cgt_xflush<<<c.grid(), kBlock, 0, c.s>>>(a);
+  a.n_active = c.w.n_active;
+  k_cgt_xflush<<<dim3(res_grid(c.L)), kBlock, 0, c.s>>>(a);
   return launched(c.st, "cgt_xflush");
 }
 

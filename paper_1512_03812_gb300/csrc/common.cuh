@@ -43,19 +43,35 @@ struct Site {
   bool valid;
 };
 
-__device__ __forceinline__ Site site_of(const Geo& g, const ChainInfo& ci, int c) {
+// Marks a chain of a grid-wide mixed solve as due a reliable update and
+// counts it in due[0] (the kernels of the update return at once while that
+// count is zero).  Called by the one thread that finishes the chain's
+// iteration.
+template <typename Chain>
+__device__ __forceinline__ void mark_update(Chain* cc, int* due) {
+  if (!cc->need_update) {
+    cc->need_update = 1;
+    atomicAdd(due, 1);
+  }
+}
+
+// blk: the site block (blockIdx.x, or a block index a looping kernel visits)
+__device__ __forceinline__ Site site_of(const Geo& g, const ChainInfo& ci, int c, int blk) {
   Site s;
   s.c = c;
   s.L = ci.L;
   s.T = ci.T;
   s.off = ci.off;
-  const int loc = (blockIdx.x - ci.blk0) * kBlock + threadIdx.x;
+  const int loc = (blk - ci.blk0) * kBlock + threadIdx.x;
   s.valid = loc < ci.L * ci.T;
   const int l = s.valid ? loc : 0;
   s.t = l / ci.L;
   s.x = l - s.t * ci.L;
   s.n = ci.off + l;
   return s;
+}
+__device__ __forceinline__ Site site_of(const Geo& g, const ChainInfo& ci, int c) {
+  return site_of(g, ci, c, blockIdx.x);
 }
 
 __device__ __forceinline__ long long at(const Site& s, int x, int t) {
@@ -315,12 +331,14 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
 template <int NV>
 __device__ __forceinline__ bool chain_reduce(double (&v)[NV], double* partials,
                                              unsigned* counters, const Geo& g,
-                                             const ChainInfo& ci, int c, double (&tot)[NV]) {
+                                             const ChainInfo& ci, int c, double (&tot)[NV],
+                                             int blk = -1) {
   __shared__ bool last;
+  if (blk < 0) blk = blockIdx.x;  // the site block whose partials these are
   block_sum<NV>(v);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) __stcg(partials + (size_t)k * g.nblocks + blockIdx.x, v[k]);
+    for (int k = 0; k < NV; ++k) __stcg(partials + (size_t)k * g.nblocks + blk, v[k]);
     __threadfence();
     const unsigned prev = atomicAdd(counters + c, 1u);
     last = (prev == (unsigned)ci.nblk - 1u);

@@ -95,7 +95,7 @@ struct Ws {
   double* out;         // [8][nchains]
   int* flags;          // [nchains] per-chain masks
   int* acc;            // [3][nchains] accumulated CG flags, iterations, reliable updates (deferred)
-  int* n_active;       // [1]
+  int* n_active;       // [2]: chains still iterating, chains due a reliable update
   int* h_n_active;     // not in ws: pinned host word (see Ctx)
 
   static size_t bytes(const sm_lattice* L);
@@ -202,6 +202,14 @@ int tiled_cg_flush(Ctx& c, float* x, const float* pa, const float* pb,
 // Kernel times of deferred solves and their site-iterations (solver.cu);
 // call after the stream has been synchronised.
 int profile_collect_deferred(const sm_lattice* L, const int* chain_iters);
+
+// Blocks of the kernels that run after every chunk of CG iterations but
+// work only when a reliable update is due (k_cg_res_d, k_cg_res_r,
+// k_cgt_xflush): each loops over site blocks, so a chunk without an update
+// costs a flag read per site block rather than a launch of every block.
+inline unsigned res_grid(const sm_lattice* L) {
+  return (unsigned)(L->nblocks < 2048 ? L->nblocks : 2048);
+}
 
 // CG on D^dag D (solver.cu).  b, x FP64; x is overwritten.  If iters/relres
 // are non-NULL they receive host copies.  Synchronises (except in deferred

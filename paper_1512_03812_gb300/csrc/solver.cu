@@ -51,7 +51,7 @@ struct CgArgs {
   CgChain* cgc;
   double* partials;
   unsigned* counters;
-  int* n_active;
+  int* n_active;  // [0] chains still iterating, [1] chains due a reliable update
   double tol2, delta2;
   int maxit;
   int mixed;
@@ -185,9 +185,9 @@ __global__ void __launch_bounds__(kBlock) k_cg_b(Geo g, CgArgs<R> a) {
     } else if (a.mixed) {
       if (conv || cc->iters >= a.maxit) {
         cc->state = 2;  // wait for the FP64 check
-        cc->need_update = 1;
+        mark_update(cc, a.n_active + 1);
       } else if (rr < a.delta2 * cc->rmax) {
-        cc->need_update = 1;
+        mark_update(cc, a.n_active + 1);
       }
       cc->rmax = fmax(cc->rmax, rr);
     } else if (conv) {
@@ -205,22 +205,30 @@ __global__ void __launch_bounds__(kBlock) k_cg_b(Geo g, CgArgs<R> a) {
 // reliable update (all chains if `all`).  x may be NULL.
 __global__ void __launch_bounds__(kBlock) k_cg_res_d(Geo g, CgArgs<float> a, const double* xhi,
                                                      const float* x, int all) {
-  CHAIN_PROLOGUE
-  if (a.grid_mask && !a.grid_mask[c_]) return;
-  if (!all && !cc->need_update) return;
-  const Site s = site_of(g, ci, c_);
-  if (!s.valid) return;
-  auto X = [&](long long m) {
-    Sp<double> v = ld_sp(xhi, m);
-    if (x) v = v + to_d(ld_sp(x, m));
-    return v;
-  };
-  const long long nxm = at(s, xm1(s), s.t), ntm = at(s, s.x, tm1(s));
-  const Lk<double> u = ld_lk(a.U64, s.n);
-  const Sp<double> o =
-      hop_sum<false, double>(X(at(s, xp1(s), s.t)), X(nxm), X(at(s, s.x, tp1(s))), X(ntm), u.x,
-                             ld_lk(a.U64, nxm).x, u.t, ld_lk(a.U64, ntm).t);
-  st_sp(a.t64, s.n, (2.0 + ci.m0) * X(s.n) - 0.5 * o);
+  // runs after every chunk of iterations: with no chain due an update (most
+  // chunks) every block returns after one read; otherwise a block visits the
+  // site blocks blockIdx.x, + gridDim.x, ...
+  if (!all && a.n_active[1] == 0) return;
+  for (int blk = blockIdx.x; blk < g.nblocks; blk += gridDim.x) {
+    const int c_ = g.blk_chain[blk];
+    if (a.grid_mask && !a.grid_mask[c_]) continue;
+    const CgChain* cc = a.cgc + c_;
+    if (!all && !cc->need_update) continue;
+    const ChainInfo ci = g.chains[c_];
+    const Site s = site_of(g, ci, c_, blk);
+    if (!s.valid) continue;
+    auto X = [&](long long m) {
+      Sp<double> v = ld_sp(xhi, m);
+      if (x) v = v + to_d(ld_sp(x, m));
+      return v;
+    };
+    const long long nxm = at(s, xm1(s), s.t), ntm = at(s, s.x, tm1(s));
+    const Lk<double> u = ld_lk(a.U64, s.n);
+    const Sp<double> o =
+        hop_sum<false, double>(X(at(s, xp1(s), s.t)), X(nxm), X(at(s, s.x, tp1(s))), X(ntm), u.x,
+                               ld_lk(a.U64, nxm).x, u.t, ld_lk(a.U64, ntm).t);
+    st_sp(a.t64, s.n, (2.0 + ci.m0) * X(s.n) - 0.5 * o);
+  }
 }
 
 // FP64 residual, step 2: r = b - D^dag t64 and |r|^2.  In update mode
@@ -228,51 +236,57 @@ __global__ void __launch_bounds__(kBlock) k_cg_res_d(Geo g, CgArgs<float> a, con
 // report mode only rr_true is written.
 __global__ void __launch_bounds__(kBlock) k_cg_res_r(Geo g, CgArgs<float> a, double* xhi,
                                                      int all) {
-  CHAIN_PROLOGUE
-  if (a.grid_mask && !a.grid_mask[c_]) return;
-  if (!all && !cc->need_update) return;
-  const Site s = site_of(g, ci, c_);
-  double v[1] = {0.0};
-  if (s.valid) {
-    const long long nxm = at(s, xm1(s), s.t), ntm = at(s, s.x, tm1(s));
-    const Lk<double> u = ld_lk(a.U64, s.n);
-    const Sp<double> o =
-        hop_sum<true, double>(ld_sp(a.t64, at(s, xp1(s), s.t)), ld_sp(a.t64, nxm),
-                              ld_sp(a.t64, at(s, s.x, tp1(s))), ld_sp(a.t64, ntm), u.x,
-                              ld_lk(a.U64, nxm).x, u.t, ld_lk(a.U64, ntm).t);
-    const Sp<double> Ax = (2.0 + ci.m0) * ld_sp(a.t64, s.n) - 0.5 * o;
-    const Sp<double> r = ld_sp(a.b, s.n) - Ax;
-    v[0] = norm2(r);
-    if (!all) {
-      st_sp(xhi, s.n, ld_sp_cg(xhi, s.n) + to_d(ld_sp_cg(a.x, s.n)));
-      st_sp(a.x, s.n, Sp<float>{{0, 0}, {0, 0}});
-      st_sp(a.r, s.n, to_r<float>(r));
+  if (!all && a.n_active[1] == 0) return;  // as k_cg_res_d
+  for (int blk = blockIdx.x; blk < g.nblocks; blk += gridDim.x) {
+    const int c_ = g.blk_chain[blk];
+    if (a.grid_mask && !a.grid_mask[c_]) continue;
+    CgChain* cc = a.cgc + c_;
+    if (!all && !cc->need_update) continue;
+    const ChainInfo ci = g.chains[c_];
+    const Site s = site_of(g, ci, c_, blk);
+    double v[1] = {0.0};
+    if (s.valid) {
+      const long long nxm = at(s, xm1(s), s.t), ntm = at(s, s.x, tm1(s));
+      const Lk<double> u = ld_lk(a.U64, s.n);
+      const Sp<double> o =
+          hop_sum<true, double>(ld_sp(a.t64, at(s, xp1(s), s.t)), ld_sp(a.t64, nxm),
+                                ld_sp(a.t64, at(s, s.x, tp1(s))), ld_sp(a.t64, ntm), u.x,
+                                ld_lk(a.U64, nxm).x, u.t, ld_lk(a.U64, ntm).t);
+      const Sp<double> Ax = (2.0 + ci.m0) * ld_sp(a.t64, s.n) - 0.5 * o;
+      const Sp<double> r = ld_sp(a.b, s.n) - Ax;
+      v[0] = norm2(r);
+      if (!all) {
+        st_sp(xhi, s.n, ld_sp_cg(xhi, s.n) + to_d(ld_sp_cg(a.x, s.n)));
+        st_sp(a.x, s.n, Sp<float>{{0, 0}, {0, 0}});
+        st_sp(a.r, s.n, to_r<float>(r));
+      }
     }
-  }
-  double tot[1];
-  if (chain_reduce<1>(v, a.partials, a.counters, g, ci, c_, tot) && threadIdx.x == 0) {
-    const double rr = tot[0];
-    cc->rr_true = rr;
-    if (!all) {
-      cc->need_update = 0;
-      cc->updates += 1;
-      cc->alpha_x = 0.0;  // x (with any pending update) is now in xhi
-      cc->rmax = rr;
-      if (!isfinite(rr)) {
-        cc->flags |= 2;
-        cc->state = 0;
-        atomicSub(a.n_active, 1);
-      } else if (rr <= a.tol2 * cc->bb) {
-        cc->state = 0;
-        atomicSub(a.n_active, 1);
-      } else if (cc->iters >= a.maxit) {
-        cc->flags |= 1;
-        cc->state = 0;
-        atomicSub(a.n_active, 1);
-      } else {
-        cc->beta = rr / cc->rr_prev;
-        cc->rr = rr;
-        cc->state = 1;
+    double tot[1];
+    if (chain_reduce<1>(v, a.partials, a.counters, g, ci, c_, tot, blk) && threadIdx.x == 0) {
+      const double rr = tot[0];
+      cc->rr_true = rr;
+      if (!all) {
+        cc->need_update = 0;
+        atomicSub(a.n_active + 1, 1);
+        cc->updates += 1;
+        cc->alpha_x = 0.0;  // x (with any pending update) is now in xhi
+        cc->rmax = rr;
+        if (!isfinite(rr)) {
+          cc->flags |= 2;
+          cc->state = 0;
+          atomicSub(a.n_active, 1);
+        } else if (rr <= a.tol2 * cc->bb) {
+          cc->state = 0;
+          atomicSub(a.n_active, 1);
+        } else if (cc->iters >= a.maxit) {
+          cc->flags |= 1;
+          cc->state = 0;
+          atomicSub(a.n_active, 1);
+        } else {
+          cc->beta = rr / cc->rr_prev;
+          cc->rr = rr;
+          cc->state = 1;
+        }
       }
     }
   }
@@ -360,10 +374,11 @@ static int residual(Ctx& c, CgArgs<float>& a, double* xhi, const float* x, int a
     const int rc = tiled_cg_flush(c, a.x, a.pa, a.pb, a.grid_mask);
     if (rc) return rc;
   }
-  k_cg_res_d<<<c.grid(), kBlock, 0, c.s>>>(c.g, a, xhi, x, all);
+  const dim3 grid(res_grid(c.L));
+  k_cg_res_d<<<grid, kBlock, 0, c.s>>>(c.g, a, xhi, x, all);
   int rc = launched(c.st, "cg_res_d");
   if (rc) return rc;
-  k_cg_res_r<<<c.grid(), kBlock, 0, c.s>>>(c.g, a, xhi, all);
+  k_cg_res_r<<<grid, kBlock, 0, c.s>>>(c.g, a, xhi, all);
   return launched(c.st, "cg_res_r");
 }
 
@@ -450,7 +465,7 @@ int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, doubl
   // the chain-resident mixed kernels compute D x of the result
   double* dxk = chain && mixed ? dx : nullptr;
 
-  SM_CU(cudaMemsetAsync(c.w.n_active, 0, sizeof(int), c.s));
+  SM_CU(cudaMemsetAsync(c.w.n_active, 0, 2 * sizeof(int), c.s));
   long long batched = 0, updates = 0;
   int rc;
   const int chunk = 8;
