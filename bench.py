@@ -238,9 +238,11 @@ def run_ours(args):
     lat = P.Lattice([L] * B, [T] * B, W["beta"], m0, device=dev)
     N = lat.N
     W = dict(W, n=args.n, M=args.M, cg_delta=args.delta)
+    if args.sf_start != "solve":
+        W["sf_start"] = args.sf_start
     cgp = P.CG(tol=W["cg_tol"], maxit=20000, prec=args.prec, delta=args.delta, algo=args.algo)
     md = P.MD(scheme=W["scheme"], tau=W["tau"], n=W["n"], M=W["M"], fg=W["fg"], cg=cgp,
-              tol_action=W["cg_tol_action"])
+              tol_action=W["cg_tol_action"], sf_start=args.sf_start)
     gen = torch.Generator(device=dev)
     gen.manual_seed(shard(world, rank, B)["seed"])
 
@@ -389,7 +391,7 @@ def run_ours(args):
     if args.fp64_steps > 0:
         md64 = P.MD(scheme=W["scheme"], tau=W["tau"], n=W["n"], M=W["M"], fg=W["fg"],
                     cg=P.CG(tol=W["cg_tol"], maxit=20000, prec="f64", algo=args.algo),
-                    tol_action=W["cg_tol_action"])
+                    tol_action=W["cg_tol_action"], sf_start=args.sf_start)
         q64 = q_start.clone()
         qm = q_start.clone()
         dev_max = 0.0
@@ -425,7 +427,8 @@ def run_ours(args):
                 return P.MD(scheme=W["scheme"], tau=W["tau"], n=W["n"], M=W["M"], fg=W["fg"],
                             cg=P.CG(tol=args.tight_tol, maxit=50000, prec=prec, algo=args.algo,
                                     delta=args.delta),
-                            tol_action=min(args.tight_tol, W["cg_tol_action"]))
+                            tol_action=min(args.tight_tol, W["cg_tol_action"]),
+                            sf_start=args.sf_start)
             qa, qb = q_start.clone(), q_start.clone()
             da, _, aa = lat.hmc_trajectory(qa, pk[0], ek[0], uk[0], md_at("f64"), check=False)
             db, _, ab = lat.hmc_trajectory(qb, pk[0], ek[0], uk[0], md_at("mixed"), check=False)
@@ -982,6 +985,9 @@ def main():
     ap.add_argument("--delta", type=float, default=0.001,
                     help="reliable-update factor of the mixed CG")
     ap.add_argument("--algo", default="auto", choices=["auto", "grid", "chain"])
+    ap.add_argument("--sf-start", default="solve", choices=["solve", "noise"],
+                    help="S_F in H at the start of a trajectory: a CG solve (default) or "
+                         "eta^dag eta, exact for phi = D^dag eta (one solve fewer)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -90,6 +90,10 @@ extern "C" {
 
 typedef struct sm_lattice sm_lattice;
 
+/* S_F at the start of a trajectory (sm_md_params.sf_start) */
+#define SM_SF_SOLVE 0
+#define SM_SF_NOISE 1
+
 /* how a batched CG solve is laid out on the GPU */
 #define SM_CG_AUTO 0   /* chain-resident when every chain fits, else grid-wide */
 #define SM_CG_GRID 1   /* all chains advance together, two launches per iteration */
@@ -129,6 +133,9 @@ typedef struct {
   sm_cg_params cg;
   double tol_action;  /* CG tolerance of the S_F solves of H in sm_hmc_trajectory
                          (0: cg.tol); the MD force solves use cg.tol */
+  int sf_start;       /* S_F in H at the start of sm_hmc_trajectory: SM_SF_SOLVE (a CG
+                         solve, like the end) or SM_SF_NOISE (eta^dag eta, exact for
+                         phi = D^dag eta; one solve fewer) */
 } sm_md_params;
 
 /* Counters accumulated over one call (zeroed by the call). */

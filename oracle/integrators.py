@@ -211,14 +211,20 @@ class TrajectoryResult:
 def hmc_trajectory(lat: sw.Lattice, q0: np.ndarray, p0: np.ndarray, eta: np.ndarray,
                    u: float, scheme: str, tau: float, n: int, M: int = 1,
                    lam: float = 1.0 / 6.0, fg: str = "exact",
-                   solver: sw.Solver | None = None) -> TrajectoryResult:
+                   solver: sw.Solver | None = None, sf_start: str = "solve") -> TrajectoryResult:
     """One HMC update (Sec. 2.1): pseudofermion heatbath phi = D^dag eta at
     the starting links, MD trajectory of length tau, Metropolis accept
     with probability min(1, e^{-Delta H}) decided as u < exp(-Delta H) for
-    a supplied uniform u in [0, 1)."""
+    a supplied uniform u in [0, 1).  sf_start = "noise" takes S_F at the
+    start as eta^dag eta, which phi^dag (D^dag D)^{-1} phi equals exactly
+    for phi = D^dag eta, instead of solving for it."""
     solver = solver or sw.Solver()
     phi = sw.apply_D(lat, sw.links(q0), eta, dagger=True)
-    H0 = sw.hamiltonian(lat, q0, p0, phi, solver)
+    if sf_start == "noise":
+        U0 = sw.links(q0)
+        H0 = sw.kinetic(p0) + sw.gauge_action(lat, U0) + float(np.vdot(eta, eta).real)
+    else:
+        H0 = sw.hamiltonian(lat, q0, p0, phi, solver)
     st = State(lat, q0.copy(), p0.copy(), phi, solver)
     md_trajectory(st, scheme, tau, n, M, lam, fg)
     H1 = sw.hamiltonian(lat, st.q, st.p, phi, solver)

@@ -60,7 +60,8 @@ class CgParams(ctypes.Structure):
 class MdParams(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int), ("tau", ctypes.c_double), ("n", ctypes.c_int),
                 ("M", ctypes.c_int), ("lambda_", ctypes.c_double), ("fg", ctypes.c_int),
-                ("merge_kicks", ctypes.c_int), ("cg", CgParams), ("tol_action", ctypes.c_double)]
+                ("merge_kicks", ctypes.c_int), ("cg", CgParams), ("tol_action", ctypes.c_double),
+                ("sf_start", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -197,12 +198,14 @@ class MD:
     merge_kicks: bool = True
     cg: CG = None
     tol_action: float = 0.0  # tolerance of the S_F solves of H (0: cg.tol)
+    sf_start: str = "solve"  # S_F at the start of a trajectory: "solve" or "noise" (eta^dag eta)
 
     def c(self) -> MdParams:
         cg = self.cg or CG()
         return MdParams(SCHEMES[self.scheme], self.tau, self.n, self.M, self.lam,
                         {"exact": FG_EXACT, "shifted": FG_SHIFTED}[self.fg],
-                        1 if self.merge_kicks else 0, cg.c(), self.tol_action)
+                        1 if self.merge_kicks else 0, cg.c(), self.tol_action,
+                        {"solve": 0, "noise": 1}[self.sf_start])
 
 
 class Lattice:

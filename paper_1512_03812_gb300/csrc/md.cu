@@ -225,6 +225,8 @@ static int check_md(const sm_md_params* md) {
     return fail(SM_ERR_ARG, "unknown scheme %d", md->scheme);
   if (md->M < 1) return fail(SM_ERR_ARG, "M = %d < 1", md->M);
   if (md->fg != SM_FG_EXACT && md->fg != SM_FG_SHIFTED) return fail(SM_ERR_ARG, "bad fg mode");
+  if (md->sf_start != SM_SF_SOLVE && md->sf_start != SM_SF_NOISE)
+    return fail(SM_ERR_ARG, "bad sf_start %d", md->sf_start);
   return check_cg(&md->cg);
 }
 
@@ -448,8 +450,13 @@ static int hmc_enqueue(Ctx& c, double* q, const double* p0, const double* eta,
   SM_TRY(launch_dslash<double>(c, c.w.U64, eta, c.w.phi, true, nullptr, 0.0));
   SM_CU(cudaMemcpyAsync(c.w.qsave, q, lbytes, cudaMemcpyDeviceToDevice, c.s));
   SM_CU(cudaMemcpyAsync(c.w.pw, p0, lbytes, cudaMemcpyDeviceToDevice, c.s));
-  SM_TRY(cg_solve(c, c.w.U64, c.w.U32, c.w.phi, c.w.xi, cgH, nullptr, nullptr));
-  SM_TRY(launch_energies(c, q, c.w.pw, c.w.phi, c.w.xi, out, out + nc, out + 2 * nc));
+  if (md.sf_start == SM_SF_NOISE) {
+    // S_F = phi^dag (D^dag D)^{-1} phi = eta^dag eta for phi = D^dag eta
+    SM_TRY(launch_energies(c, q, c.w.pw, eta, eta, out, out + nc, out + 2 * nc));
+  } else {
+    SM_TRY(cg_solve(c, c.w.U64, c.w.U32, c.w.phi, c.w.xi, cgH, nullptr, nullptr));
+    SM_TRY(launch_energies(c, q, c.w.pw, c.w.phi, c.w.xi, out, out + nc, out + 2 * nc));
+  }
   SM_TRY(md_run(c, q, c.w.pw, c.w.phi, md, md.tau / md.n, md.n));
   SM_TRY(make_links(c, q, c.w.U64, c.w.U32, cg));
   SM_TRY(cg_solve(c, c.w.U64, c.w.U32, c.w.phi, c.w.xi, cgH, nullptr, nullptr));

@@ -211,6 +211,33 @@ def test_column_pair_variants_need_64x64_chains(torch):
     assert (relres <= 1e-10).all(), relres
 
 
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_hmc_sf_start_from_noise(torch, prec):
+    """sf_start = "noise" (S_F at the start = eta^dag eta): one CG solve fewer
+    per trajectory, Delta H and the decisions as the oracle's with the same
+    option, and as the library's two-solve form to the solver's tolerance."""
+    import paper_1512_03812_gb300 as P
+    b = batch(torch)
+    q, p, eta = b.q(), b.p(), b.eta()
+    u = np.full(len(b.dims), 0.5)
+    res = {}
+    for sf in ("solve", "noise"):
+        md = P.MD(scheme="adapted_nested_fg", tau=0.5, n=2, M=2,
+                  cg=P.CG(tol=1e-13, prec=prec, delta=0.01), sf_start=sf)
+        dH, H0, acc = b.lat.hmc_trajectory(b.dev(q), b.dev(p), b.dev(eta), u, md)
+        res[sf] = (dH, H0, acc, b.lat.stats.as_dict()["cg_solves"])
+    assert res["noise"][3] == res["solve"][3] - 1
+    for c, ol in enumerate(b.olat):
+        ro = ig.hmc_trajectory(ol, b.chain(q, c), b.chain(p, c), b.chain(eta, c), 0.5,
+                               "adapted_nested_fg", 0.5, 2, M=2, solver=sw.Solver(1e-14),
+                               sf_start="noise")
+        dH, H0, acc, _ = res["noise"]
+        assert abs(H0[c] - ro.H0) < 1e-9 * abs(ro.H0)
+        assert abs(dH[c] - ro.dH) < 1e-8, (c, dH[c], ro.dH)
+        assert bool(acc[c]) == ro.accepted
+        assert abs(res["solve"][0][c] - dH[c]) < 1e-8
+
+
 def test_mixed_batch_with_128x128_chains(torch):
     """A batch of small chains and 128 x 128 chains is solved chain-resident
     throughout: the small ones one block each, the large ones by 4-block

@@ -338,6 +338,25 @@ def test_metropolis_decision():
     assert r0.accepted
 
 
+def test_sf_start_from_noise_matches_the_solve():
+    """H at the start with S_F = eta^dag eta (exact for phi = D^dag eta)
+    against S_F = phi^dag (D^dag D)^{-1} phi by CG: the same trajectory, H0
+    and Delta H equal to the solver's tolerance, the same decision."""
+    lat, q, _ = setup(4, 6, beta=2.0, kappa=0.22)
+    p = field(I.momenta(4, 6, 5), 4, 6)
+    eta = field(I.noise(4, 6, 6), 4, 6)
+    a = ig.hmc_trajectory(lat, q, p, eta, 0.5, "leapfrog", 1.0, 4, solver=sw.Solver(1e-14))
+    b = ig.hmc_trajectory(lat, q, p, eta, 0.5, "leapfrog", 1.0, 4, solver=sw.Solver(1e-14),
+                          sf_start="noise")
+    assert abs(a.H0 - b.H0) < 1e-10 * abs(a.H0)
+    assert abs(a.dH - b.dH) < 1e-10 * abs(a.H0)
+    assert np.array_equal(a.q_md, b.q_md) and a.accepted == b.accepted
+    # the identity it rests on, on a random field: phi^dag (D^dag D)^-1 phi = |eta|^2
+    U = sw.links(q)
+    phi = sw.apply_D(lat, U, eta, dagger=True)
+    assert abs(sw.fermion_action(lat, U, phi, sw.Solver(1e-14)) - np.vdot(eta, eta).real) < 1e-10
+
+
 def test_creutz_equality_on_markov_chain():
     """<exp(-Delta H)> = 1 in equilibrium (a consequence of reversibility and
     area preservation, Sec. 2.2), checked on an oracle HMC chain."""
