@@ -44,3 +44,39 @@ def test_error_path_without_gpu_work():
     rc = lib.sm_lattice_create(0, None, None, None, None, ctypes.byref(h))
     assert rc == 1 and b"nchains" in lib.sm_last_error()
     assert lib.sm_lattice_destroy(None) == 0
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the sizes and field offsets that a
+    C compiler gives the header's structs (compiled with gcc, no GPU)."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1512_03812_gb300 import binding as B
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"sm_cg_params": B.CgParams, "sm_md_params": B.MdParams, "sm_stats": B.Stats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "schwinger.h"',
+             "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            cf = "lambda" if f == "lambda_" else f
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {cf}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c = {}
+    for line in out:
+        if line:
+            name, key, val = line.split()
+            c[(name, key)] = int(val)
+    for cname, py in structs.items():
+        assert c[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert c[(cname, f)] == getattr(py, f).offset, (cname, f)
