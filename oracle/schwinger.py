@@ -4,8 +4,8 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``): a plain FP64 numpy
 restatement of Sec. 3 of "Adapted nested force-gradient integrators: the
 Schwinger model case" (arXiv:1512.03812).  Shares no code with the CUDA path.
 
-Conventions (readings of the paper are listed in the design doc)
------------------------------------------------------------
+Conventions (where the paper is silent, the reading taken is stated here)
+-------------------------------------------------------------------------
 * A lattice is L (space, x, paper direction mu=1) by T (time, t, paper
   mu=2).  Every field is a numpy array of shape (T, L, ...): site
   n = (x, t) sits at [t, x], so the C-order flattening is n = x + L*t.
