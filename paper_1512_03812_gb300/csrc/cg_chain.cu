@@ -1301,6 +1301,29 @@ bool chain_cg_selected(const sm_lattice* L, const sm_cg_params& cg) {
   return cg.algo == SM_CG_CHAIN ? fits : (cg.algo == SM_CG_AUTO && fits);
 }
 
+// The chains of `list` in order of decreasing iteration count of their last
+// solve (ties by position).  A launch with one block per chain over this
+// order starts the longest chains first and gives the SMs that free up the
+// shorter ones (blocks are dispatched in index order): consecutive solves on
+// similar links take similar iteration counts, so the last wave's idle tail
+// shrinks.  The counts are only a guess (any values give a permutation of
+// `list`, and a chain's result does not depend on its block).  One block:
+// the counts are staged in shared memory (n <= kOrderMax).
+constexpr int kOrderMax = 8192;
+__global__ void __launch_bounds__(1024) k_chain_order(const CgChain* __restrict__ cgc,
+                                                      const int* __restrict__ list,
+                                                      int* __restrict__ out, int n) {
+  __shared__ int key[kOrderMax];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) key[j] = cgc[list[j]].iters;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int ki = key[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) rank += (key[j] > ki) || (key[j] == ki && j < i);
+    out[rank] = list[i];
+  }
+}
+
 // Deferred mode: acc[c] |= flags, acc[nchains + c] += iterations,
 // acc[2 nchains + c] += reliable updates.
 __global__ void k_cg_accumulate(const CgChain* __restrict__ cgc, int* acc, int nchains) {
@@ -1423,10 +1446,19 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
       go(k_cg_chain_col<8, 512>, 512);
     } else if (v == 2) {
       go(k_cg_chain_col<16, 256>, 256);
-    } else if (v == 5) {
-      go(k_cg_chain_pair<4, 512, 64, 64, 1>, 512);
-    } else if (v == 6) {
-      go(k_cg_chain_pair<8, 256, 64, 64, 1>, 256);
+    } else if (v == 5 || v == 6) {
+      // one block per chain, the chains longest first (k_chain_order)
+      const int n = L->nchains;
+      ChainCgArgs ao = a;
+      if (n <= kOrderMax) {
+        k_chain_order<<<1, 1024, 0, c.s>>>(c.w.cgc, L->d_chain_list, c.w.order, n);
+        const int rc = launched(c.st, "chain_order");
+        if (rc) return rc;
+        ao.list = c.w.order;
+      }
+      auto kern = v == 5 ? k_cg_chain_pair<4, 512, 64, 64, 1> : k_cg_chain_pair<8, 256, 64, 64, 1>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) kern<<<grid, dim3(v == 5 ? 512 : 256), smem, c.s>>>(ao);
     } else if (v == 7) {
       e = launch_cluster<2>(k_cg_chain_pair<8, 128, 64, 64, 2>, L->nchains, 128, smem / 2, c.s, a);
     } else if (vmax <= 1024) {

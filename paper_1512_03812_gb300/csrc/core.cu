@@ -62,6 +62,7 @@ size_t Ws::bytes(const sm_lattice* L) {
   b += align256(nc * sizeof(int));
   b += align256(3 * nc * sizeof(int));
   b += align256(2 * sizeof(int));
+  b += align256(nc * sizeof(int));
   return b;
 }
 
@@ -95,6 +96,7 @@ int Ws::carve(const sm_lattice* L, void* ws, size_t nbytes) {
   flags = reinterpret_cast<int*>(take(nc * sizeof(int)));
   acc = reinterpret_cast<int*>(take(3 * nc * sizeof(int)));
   n_active = reinterpret_cast<int*>(take(2 * sizeof(int)));
+  order = reinterpret_cast<int*>(take(nc * sizeof(int)));
   h_n_active = L->h_pinned;
   return SM_OK;
 }

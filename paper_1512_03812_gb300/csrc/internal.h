@@ -96,6 +96,7 @@ struct Ws {
   int* flags;          // [nchains] per-chain masks
   int* acc;            // [3][nchains] accumulated CG flags, iterations, reliable updates (deferred)
   int* n_active;       // [2]: chains still iterating, chains due a reliable update
+  int* order;          // [nchains] chains, longest previous solve first
   int* h_n_active;     // not in ws: pinned host word (see Ctx)
 
   static size_t bytes(const sm_lattice* L);

@@ -59,3 +59,49 @@ def test_graph_needs_chain_resident_solves(torch):
     md = P.MD(scheme="leapfrog", tau=0.2, n=2, cg=P.CG(tol=1e-10, prec="mixed", algo="grid"))
     with pytest.raises(P.SchwingerError):
         b.lat.hmc_graph(q, b.dev(b.p()), b.dev(b.eta()), md)
+
+
+def test_graph_equals_eager_longest_first(torch):
+    """160 chains of 64 x 64 on the column-pair kernel pinned (variant 6):
+    its launches take the chains in the order of their previous solve's
+    iteration counts, which changes between solves; the results do not
+    depend on it (graph and eager bitwise equal, and a chain's solution equal
+    to that of the same chain solved alone)."""
+    import paper_1512_03812_gb300 as P
+    n = 160
+    b = Batch([(64, 64)] * n, 2.0, 0.24, seed=14)
+    b.lat.set_cg_variant(6)
+    md = P.MD(scheme="adapted_nested_fg", tau=0.25, n=1, M=2,
+              cg=P.CG(tol=1e-10, prec="mixed", delta=0.01), tol_action=1e-12)
+    q0 = b.q()
+    ps = [b.p(40 + k) for k in range(2)]
+    es = [b.eta(50 + k) for k in range(2)]
+    rng = np.random.default_rng(3)
+    us = [rng.random(n) for _ in range(2)]
+    qe = b.dev(q0)
+    eager = [b.lat.hmc_trajectory(qe, b.dev(ps[k]), b.dev(es[k]), us[k], md, check=False)
+             for k in range(2)]
+    qg = b.dev(q0)
+    p0 = torch.empty_like(b.dev(ps[0]))
+    eta = torch.empty_like(b.dev(es[0]))
+    g = b.lat.hmc_graph(qg, p0, eta, md)
+    for k in range(2):
+        p0.copy_(b.dev(ps[k]))
+        eta.copy_(b.dev(es[k]))
+        dH, H0, acc = g.run(us[k])
+        assert np.array_equal(dH, eager[k][0])
+        assert np.array_equal(acc, eager[k][2])
+    torch.cuda.synchronize()
+    assert torch.equal(qg, qe)
+    # chain c's result is the same when it is solved alone
+    one = Batch([(64, 64)], 2.0, 0.24, seed=14)
+    one.lat.set_cg_variant(6)
+    U64, U32 = b.lat.links(b.dev(q0))
+    phi = b.dev(b.spinor())
+    x, _, _ = b.lat.cg_solve(U64, U32, phi, P.CG(tol=1e-10, prec="mixed", delta=0.01))
+    c = 137
+    sl = slice(b.off[c], b.off[c + 1])
+    U64c, U32c = one.lat.links(b.dev(q0)[sl].contiguous())
+    xc, _, _ = one.lat.cg_solve(U64c, U32c, phi[sl].contiguous(),
+                                P.CG(tol=1e-10, prec="mixed", delta=0.01))
+    assert torch.equal(x[sl], xc)
