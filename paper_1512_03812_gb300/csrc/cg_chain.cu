@@ -1414,6 +1414,12 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
     bool sq128 = true;  // all large chains 128 x 128: the column-pair form
     for (const ChainInfo& ci : L->chains)
       if (ci.L * ci.T > kChainMaxVolume) sq128 = sq128 && ci.L == 128 && ci.T == 128;
+    if (sq128 && L->nbig <= kOrderMax) {
+      // the clusters longest first, as for the one-block column pairs
+      k_chain_order<<<1, 1024, 0, c.s>>>(c.w.cgc, L->d_big_list, c.w.order, L->nbig);
+      if ((rc = launched(c.st, "chain_order"))) return rc;
+      ab.list = c.w.order;
+    }
     if (sq128)
       e = launch_cluster<4>(k_cg_chain_pair<8, 256, 128, 128, 4>, L->nbig, 256,
                             (size_t)3 * 4096 * 16, c.s, ab);
