@@ -605,12 +605,14 @@ def run_other(args):
         accs = []
         for p, e, u in draws:
             flush.fill_(1)
+            torch.cuda.nvtx.range_push("timed_step")  # lets ncu select the timed steps
             if eager:
                 _, _, acc = lat.hmc_trajectory(q, p, e, u, md, check=False)
             else:
                 p_buf.copy_(p)
                 e_buf.copy_(e)
                 _, _, acc = graph.run(u)
+            torch.cuda.nvtx.range_pop()
             accs.append(acc)
         e1.record()
         torch.cuda.synchronize()
