@@ -42,7 +42,7 @@ WORKLOAD = {
                 "mixed-precision CG tol 1e-10 (1e-12 for the S_F of H)",
     "L": 64, "T": 64, "beta": 2.0, "kappa": 0.26, "chains_per_gpu": 304,
     "scheme": "adapted_nested_fg", "tau": 1.0, "n": 8, "M": 2, "fg": "exact",
-    "cg_tol": 1e-10, "cg_tol_action": 1e-12, "cg_delta": 0.001, "precision": "mixed",
+    "cg_tol": 1e-10, "cg_tol_action": 1e-12, "cg_delta": 0.0003, "precision": "mixed",
 }
 # Global-memory bytes per site and CG iteration of a memory-resident CG
 # iteration (the grid-wide pair of solver.cu: kernel A reads r, p, U and
@@ -516,11 +516,12 @@ OTHER_WORKLOADS = {
         "workload": "256 chains, sides from {16,32,48,64,128}, beta in {1,2,4}, kappa in "
                     "[0.20,0.26], adapted nested FG n=6 m=2, mixed CG tol 1e-10",
         "chains": 256, "scheme": "adapted_nested_fg", "tau": 1.0, "n": 6, "M": 2,
-        "cg_tol": 1e-10, "cg_tol_action": 1e-12, "therm": (6, 4)},
+        "cg_tol": 1e-10, "cg_tol_action": 1e-12, "cg_delta": 0.001, "therm": (6, 4)},
     "large": {
         "workload": "2048x2048 beta=8.0 kappa=0.255, adapted nested FG n=8 m=3, mixed CG tol 1e-10",
         "L": 2048, "beta": 8.0, "kappa": 0.255, "scheme": "adapted_nested_fg", "tau": 1.0,
-        "n": 8, "M": 3, "cg_tol": 1e-10, "cg_tol_action": 1e-12, "therm": (3, 2)},
+        "n": 8, "M": 3, "cg_tol": 1e-10, "cg_tol_action": 1e-12, "cg_delta": 0.001,
+        "therm": (3, 2)},
 }
 
 
@@ -700,6 +701,7 @@ def run_other(args):
 # step size of each integrator at 90 % acceptance and its inversions of D.
 PAPER = {
     "L": 32, "T": 32, "beta": 1.0, "m0": -0.231367, "tau": 2.0, "sets": 200, "M": 5,
+    "cg_delta": 0.001,
     # integrator, force-gradient form, Table 1 step size, its D^-1 per step
     # and per trajectory as printed
     "table1": [("five_stage", "exact", 0.0294, 6, 420),
@@ -985,8 +987,9 @@ def main():
                     help="thermalisation trajectories of the paper workload")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])
     ap.add_argument("--M", type=int, default=WORKLOAD["M"])
-    ap.add_argument("--delta", type=float, default=0.001,
-                    help="reliable-update factor of the mixed CG")
+    ap.add_argument("--delta", type=float, default=None,
+                    help="reliable-update factor of the mixed CG (default: the workload's, "
+                         "0.0003 for the 64x64 chains, 0.001 for the others)")
     ap.add_argument("--algo", default="auto", choices=["auto", "grid", "chain"])
     ap.add_argument("--sf-start", default="solve", choices=["solve", "noise"],
                     help="S_F in H at the start of a trajectory: a CG solve (default) or "
@@ -997,10 +1000,16 @@ def main():
     elif args.workload == "stencil":
         run_stencil(args)
     elif args.workload == "paper":
+        if args.delta is None:
+            args.delta = PAPER["cg_delta"]
         run_paper(args)
     elif args.workload != "default":
+        if args.delta is None:
+            args.delta = OTHER_WORKLOADS[args.workload]["cg_delta"]
         run_other(args)
     else:
+        if args.delta is None:
+            args.delta = WORKLOAD["cg_delta"]
         run_ours(args)
 
 
