@@ -565,3 +565,37 @@ def test_null_workspace_is_an_argument_error(torch):
     FG = b.lat.gauge_force(qd)
     for c, ol in enumerate(b.olat):
         assert rel_err(b.chain(FG, c), sw.gauge_force(ol, sw.links(b.chain(b.q(), c)))) < TOL64
+
+
+def test_mixed_delta_h_within_1e8_of_fp64_on_64x64(torch):
+    """The mixed-precision target on the bench's chain shape (64 x 64,
+    beta 2, kappa 0.26) and kernel (column pairs), on a configuration
+    thermalised by a few trajectories (heavy fermions first, then kappa 0.26
+    with small steps, all accepted): with both paths solving to a true
+    relative residual of 1e-12, Delta H of the mixed path is within 1e-8 of
+    the FP64 path's and every accept/reject decision is the same."""
+    import paper_1512_03812_gb300 as P
+    n = 8
+    one = batch(torch, dims=[(64, 64)], betas=2.0, kappas=0.10, seed=21)
+    q1 = one.dev(np.zeros_like(one.q()))
+    for k, (kap, steps, M, ntraj) in enumerate([(0.10, 5, 8, 10), (0.26, 16, 4, 6)]):
+        lat1 = P.Lattice(64, 64, 2.0, 1.0 / (2.0 * kap) - 2.0)
+        md1 = P.MD(scheme="nested_leapfrog", tau=1.0, n=steps, M=M, cg=P.CG(1e-8, 20000, "mixed"))
+        for t in range(ntraj):
+            lat1.hmc_trajectory(q1, one.dev(one.p(100 + 10 * k + t)), one.dev(one.eta(200 + 10 * k + t)),
+                                0.0, md1, check=False)
+    b = batch(torch, dims=[(64, 64)] * n, betas=2.0, kappas=0.26, seed=21)
+    b.lat.set_cg_variant(6)
+    q = np.tile(q1.cpu().numpy(), (n, 1))
+    p, eta = b.p(), b.eta()
+    us = np.linspace(0.05, 0.95, n)
+    out = {}
+    for prec in ("f64", "mixed"):
+        md = P.MD(scheme="adapted_nested_fg", tau=1.0, n=8, M=2,
+                  cg=P.CG(tol=1e-12, maxit=50000, prec=prec, delta=3e-4), tol_action=1e-12)
+        out[prec] = b.lat.hmc_trajectory(b.dev(q), b.dev(p), b.dev(eta), us, md)
+    dHf, _, accf = out["f64"]
+    dHm, _, accm = out["mixed"]
+    assert np.abs(dHf).max() < 10.0, dHf  # a sensible trajectory
+    assert np.abs(dHm - dHf).max() < 1e-8, np.abs(dHm - dHf).max()
+    assert np.array_equal(accm, accf)
