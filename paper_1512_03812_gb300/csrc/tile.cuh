@@ -67,15 +67,25 @@ __device__ __forceinline__ bool tma_stage(float4* sp, float4* su, const CUtensor
         "l"(reinterpret_cast<unsigned long long>(tU)), "r"(cx), "r"(cy), "r"(b)
         : "memory");
   }
-  unsigned done = 0;
-  for (int i = 0; i < kTmaSpin && !done; ++i)
+  auto poll = [&]() {
+    unsigned ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
+        : "=r"(ok)
         : "r"(b)
         : "memory");
-  if (!done && threadIdx.x == 0 && err) atomicOr(err, 1);
+    return ok;
+  };
+  unsigned done = 0;
+  for (int i = 0; i < kTmaSpin && !done; ++i) done = poll();
+  if (!done) {
+    if (threadIdx.x == 0 && err) atomicOr(err, 1);
+    // the copies may still be landing in this block's shared memory: wait for
+    // them (again bounded) before the block gives up its tile and exits
+    unsigned late = 0;
+    for (int i = 0; i < 16 * kTmaSpin && !late; ++i) late = poll();
+  }
   return __syncthreads_and(done) != 0;
 }
 
