@@ -80,3 +80,25 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert c[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert c[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_binding_constants_match_the_header():
+    """The binding's scheme, precision, part, force-gradient and status codes
+    and the number of chain-CG variants are the header's #defines."""
+    from paper_1512_03812_gb300 import binding as B
+    src = open(os.path.join(ROOT, "include", "schwinger.h")).read()
+    d = {k: int(v) for k, v in re.findall(r"^#define (SM_\w+) (-?\d+)", src, flags=re.M)}
+    names = {"leapfrog": "SM_LEAPFROG", "five_stage": "SM_FIVE_STAGE",
+             "five_stage_fg": "SM_FIVE_STAGE_FG", "nested_leapfrog": "SM_NESTED_LEAPFROG",
+             "nested_five_stage": "SM_NESTED_FIVE_STAGE", "nested_fg": "SM_NESTED_FG",
+             "adapted_nested_fg": "SM_ADAPTED_NESTED_FG", "eleven_stage": "SM_ELEVEN_STAGE"}
+    assert set(B.SCHEMES) == set(names)
+    for k, v in B.SCHEMES.items():
+        assert v == d[names[k]], k
+    for k in ("SM_OK", "SM_ERR_ARG", "SM_ERR_CUDA", "SM_ERR_NOT_CONVERGED", "SM_ERR_TIMEOUT",
+              "SM_ERR_NAN", "SM_F64", "SM_F32", "SM_MIXED"):
+        assert getattr(B, k) == d[k], k
+    assert (B.PART_GAUGE, B.PART_FERMION, B.PART_FULL) == (
+        d["SM_PART_GAUGE"], d["SM_PART_FERMION"], d["SM_PART_FULL"])
+    assert (B.FG_EXACT, B.FG_SHIFTED) == (d["SM_FG_EXACT"], d["SM_FG_SHIFTED"])
+    assert B.CG_VARIANTS == d["SM_CG_VARIANTS"]
