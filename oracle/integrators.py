@@ -27,6 +27,8 @@ from . import schwinger as sw
 
 @dataclass
 class State:
+    """The phase-space point (q, p) of one chain with its pseudofermion phi
+    (fixed during a trajectory, Sec. 2.1)."""
     lat: sw.Lattice
     q: np.ndarray
     p: np.ndarray
@@ -35,15 +37,22 @@ class State:
 
 
 def drift(st: State, eps: float) -> None:
+    """The link update e^{eps A}: q <- q + eps p (Sec. 2.1, U <- e^{i eps P} U
+    for U(1) link angles, reading 1)."""
     st.q = st.q + eps * st.p
 
 
 def kick(st: State, eps: float, part: str) -> None:
+    """The momentum update e^{eps B}: p <- p - eps F(q) of one part of the
+    action (Sec. 2.1; F = dS/dq, Eq. force)."""
     st.p = st.p - eps * sw.force(st.lat, sw.links(st.q), st.phi, st.solver, part)
 
 
 def fg_kick(st: State, h: float, part: str, fg: str) -> None:
-    """The force-gradient kick e^{(2/3) h B + (1/72) h^3 C} for step h."""
+    """The force-gradient kick e^{(2/3) h B + (1/72) h^3 C} for step h, the
+    middle kick of Eq. 5stage_fg (its sign as in reading 2); fg = "shifted"
+    takes the force at the shifted field instead (Sec. 2, after Eq.
+    5stage_fg)."""
     if fg == "exact":
         F, C = sw.force_and_gradient(st.lat, sw.links(st.q), st.phi, st.solver, part)
         st.p = st.p - (2.0 * h / 3.0) * F + (h ** 3 / 72.0) * C
@@ -190,7 +199,9 @@ LAMBDA_2MN = 0.1931833275037836
 
 def md_trajectory(st: State, scheme: str, tau: float, n: int, M: int = 1,
                   lam: float = 1.0 / 6.0, fg: str = "exact") -> None:
-    """n steps of size h = tau / n of one scheme."""
+    """n steps of size h = tau / n of one scheme of Sec. 2 (Eqs. leap,
+    5stage, 5stage_fg, 11_stage, leap_multi, 5stage_multi, 5stage_multi_fg,
+    ad_5stage_multi_fg)."""
     h = tau / n
     step = SCHEMES[scheme]
     for _ in range(n):

@@ -54,7 +54,8 @@ class Lattice:
 
 
 def kappa_to_m0(kappa: float) -> float:
-    """Hopping parameter to bare mass: kappa = 1 / (2 (2 + m0))."""
+    """Hopping parameter to bare mass: kappa = 1 / (2 (2 + m0)) (the paper
+    writes D with m0, Sec. 3; the configurations give kappa)."""
     return 1.0 / (2.0 * kappa) - 2.0
 
 
@@ -68,7 +69,8 @@ def shift(a: np.ndarray, mu: int, d: int) -> np.ndarray:
 def psi_shift(psi: np.ndarray, mu: int, d: int, bc: float) -> np.ndarray:
     """psi(n + d mu_hat) for a fermion field, d = +1 or -1: periodic in x,
     and in t a value brought across the t = T-1 <-> 0 boundary is
-    multiplied by ``bc``."""
+    multiplied by ``bc`` (the paper does not state the fermion boundary
+    conditions; antiperiodic in t is the reading taken)."""
     out = np.roll(psi, -d, axis=_AXIS[mu]).copy()
     if mu == 1 and bc != 1.0:
         if d == +1:
@@ -413,7 +415,7 @@ def force_and_gradient(lat: Lattice, U: np.ndarray, phi: np.ndarray, solver: Sol
 
 def force_gradient(lat: Lattice, U: np.ndarray, phi: np.ndarray, solver: Solver,
                    part: str = "full") -> np.ndarray:
-    """C alone (see ``force_and_gradient``)."""
+    """C = grad |F|^2 alone (Eq. force_gradient; see ``force_and_gradient``)."""
     return force_and_gradient(lat, U, phi, solver, part)[1]
 
 
