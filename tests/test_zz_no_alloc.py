@@ -3,7 +3,6 @@ callers that cannot call cudaMalloc and so can create neither a workspace nor
 a lattice object: its output must match the workspace-based sm_apply_DdagD,
 within the tolerances the parity tests use, on two calls in a row.  This file
 is collected last; it also passes on its own in a fresh process."""
-import numpy as np
 import pytest
 
 from oracle import schwinger as sw
