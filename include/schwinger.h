@@ -228,7 +228,10 @@ int sm_apply_DdagD(const sm_lattice* lat, const void* U, const void* in, void* o
  * are rejected with SM_ERR_ARG.  The array is loaded with the library on
  * every GPU that uses it and held until the process exits.  The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All
+ * that device current, and so does the first call after the device's context
+ * was torn down and recreated (for example by cudaDeviceReset: the address is
+ * cached with the context's unique id); make such a call before any stream
+ * capture.  All
  * calls share the one array and each overwrites it completely before reading
  * it, so nothing carries over between calls -- but calls whose work can
  * overlap on the GPU (different streams, or concurrent host threads) race on

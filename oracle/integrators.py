@@ -38,7 +38,9 @@ class State:
 
 def drift(st: State, eps: float) -> None:
     """The link update e^{eps A}: q <- q + eps p (Sec. 2.1, U <- e^{i eps P} U
-    for U(1) link angles, reading 1)."""
+    for U(1) link angles; the momentum update printed there as P - i h F is
+    read for the U(1) algebra element P = i p with p real, which gives the
+    real kick p <- p - h F with F = dS/dq of Eq. force)."""
     st.q = st.q + eps * st.p
 
 
@@ -50,9 +52,13 @@ def kick(st: State, eps: float, part: str) -> None:
 
 def fg_kick(st: State, h: float, part: str, fg: str) -> None:
     """The force-gradient kick e^{(2/3) h B + (1/72) h^3 C} for step h, the
-    middle kick of Eq. 5stage_fg (its sign as in reading 2); fg = "shifted"
+    middle kick of Eq. 5stage_fg; fg = "shifted"
     takes the force at the shifted field instead (Sec. 2, after Eq.
-    5stage_fg)."""
+    5stage_fg).  The sign of the C term: Eq. 5stage_fg prints it negative,
+    Eq. 5stage_multi_fg and Eq. ad_5stage_multi_fg positive; with C = grad |F|^2
+    of Eq. force_gradient and the kick p <- p - eps F of Sec. 2.1 the
+    composition is of fourth order only with the positive sign used here
+    (Sec. 2.1, the force-gradient step of Eq. 5stage_fg)."""
     if fg == "exact":
         F, C = sw.force_and_gradient(st.lat, sw.links(st.q), st.phi, st.solver, part)
         st.p = st.p - (2.0 * h / 3.0) * F + (h ** 3 / 72.0) * C

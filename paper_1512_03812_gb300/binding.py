@@ -426,12 +426,33 @@ class HmcGraph:
 def apply_DdagD_noalloc(L: int, T: int, m0: float, U, psi, out=None):
     """D^dag D psi for one L x T lattice through the entry point that
     allocates nothing (sm_apply_DdagD_noalloc); for callers that cannot
-    create a workspace or a lattice object."""
+    create a workspace or a lattice object.
+
+    The C side sees only pointers and the sides L, T, so the tensors are
+    checked here before anything is launched: psi of shape (L*T, 2),
+    complex128 or complex64; U (links from sm_links) and out of the same
+    shape and dtype; all three contiguous and on the current CUDA device.
+    A mismatch raises ValueError."""
+    L, T = int(L), int(T)
+    if psi.dtype not in (torch.complex128, torch.complex64):
+        raise ValueError(f"psi must be complex128 or complex64, got {psi.dtype}")
+    out = torch.empty_like(psi) if out is None else out
+    shape = (L * T, 2)
+    for name, t in (("psi", psi), ("U", U), ("out", out)):
+        if tuple(t.shape) != shape:
+            raise ValueError(f"{name} must have shape {shape} for a {L} x {T} lattice, "
+                             f"got {tuple(t.shape)}")
+        if t.dtype != psi.dtype:
+            raise ValueError(f"{name} must have psi's dtype {psi.dtype}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    for name, t in (("psi", psi), ("U", U), ("out", out)):
+        if t.device.type != "cuda" or t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} must be on the current CUDA device, got {t.device}")
     lib = load()
     prec = SM_F64 if psi.dtype == torch.complex128 else SM_F32
-    out = torch.empty_like(psi) if out is None else out
-    _check(lib.sm_apply_DdagD_noalloc(int(L), int(T), float(m0), _ptr(U), _ptr(psi), _ptr(out),
-                                      prec, _stream()))
+    _check(lib.sm_apply_DdagD_noalloc(L, T, float(m0), _ptr(U), _ptr(psi), _ptr(out), prec,
+                                      _stream()))
     return out
 
 

@@ -20,6 +20,7 @@ File format (little-endian), one file per batch:
 from __future__ import annotations
 
 import json
+import os
 import struct
 
 import numpy as np
@@ -47,12 +48,23 @@ def save(path, lattice, q, trajectory: int, rng_state=None, params: dict | None 
         "rng_bytes": len(rb),
     }
     hb = json.dumps(header, sort_keys=True).encode("utf-8")
-    with open(path, "wb") as f:
-        f.write(MAGIC)
-        f.write(struct.pack("<Q", len(hb)))
-        f.write(hb)
-        f.write(qb)
-        f.write(rb)
+    # written beside the target, flushed to disk, then renamed over it: a
+    # crash or a full disk part-way leaves the previous checkpoint intact
+    tmp = os.fspath(path) + ".tmp"
+    try:
+        with open(tmp, "wb") as f:
+            f.write(MAGIC)
+            f.write(struct.pack("<Q", len(hb)))
+            f.write(hb)
+            f.write(qb)
+            f.write(rb)
+            f.flush()
+            os.fsync(f.fileno())
+        os.replace(tmp, path)
+    except BaseException:
+        if os.path.exists(tmp):
+            os.remove(tmp)
+        raise
 
 
 def load(path) -> dict:

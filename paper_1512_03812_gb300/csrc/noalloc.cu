@@ -9,6 +9,8 @@
 // sm_lattice_create allocates the geometry tables.  The entry point below
 // takes the geometry of a single L x T lattice by value and keeps t in a
 // file-scope device array, so it allocates nothing.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -25,25 +27,69 @@ constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;
-static void* g_scratch_ptr[kMaxDevices];
+// The array's device address, per device, with the unique id of the context
+// it was looked up in.  After cudaDeviceReset (or any other teardown of the
+// primary context) the library's module is loaded again in a new context and
+// the array gets a new address: the id no longer matches and the address is
+// looked up again.
+struct ScratchAddr {
+  unsigned long long ctx_id;
+  void* ptr;
+};
+static ScratchAddr g_scratch[kMaxDevices];
 static std::mutex g_scratch_mu;
 
-// The device address of the scratch array on the current device, looked up
-// once per device (host code cannot use the array's name as an address).
+// The unique id of the calling thread's current context (driver entry
+// points, no link against the driver library); false if none is current or
+// the driver does not offer the calls.
+static bool current_context_id(unsigned long long* id) {
+  static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+  });
+  if (!get_current || !get_id) return false;
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// The device address of the scratch array on the current device (host code
+// cannot use the array's name as an address).  Looked up with
+// cudaGetSymbolAddress the first time a device's context calls, which also
+// initialises that context if the runtime has not yet; later calls in the
+// same context reuse it.  Where the context id cannot be read, every call
+// looks the address up.
 static int scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(SM_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(SM_ERR_ARG, "device ordinal %d too large", dev);
+  unsigned long long id = 0;
+  bool have_id = current_context_id(&id);
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess)
-      return fail(SM_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-    g_scratch_ptr[dev] = p;
+  if (have_id && g_scratch[dev].ptr && g_scratch[dev].ctx_id == id) {
+    *out = g_scratch[dev].ptr;
+    return SM_OK;
   }
-  *out = g_scratch_ptr[dev];
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess)
+    return fail(SM_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+  if (!have_id) have_id = current_context_id(&id);  // the lookup made the context current
+  g_scratch[dev] = have_id ? ScratchAddr{id, p} : ScratchAddr{0, nullptr};
+  *out = p;
   return SM_OK;
 }
 

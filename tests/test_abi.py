@@ -102,3 +102,26 @@ def test_binding_constants_match_the_header():
         d["SM_PART_GAUGE"], d["SM_PART_FERMION"], d["SM_PART_FULL"])
     assert (B.FG_EXACT, B.FG_SHIFTED) == (d["SM_FG_EXACT"], d["SM_FG_SHIFTED"])
     assert B.CG_VARIANTS == d["SM_CG_VARIANTS"]
+
+
+def test_noalloc_binding_refuses_mismatched_tensors_before_launching():
+    """The no-alloc entry point sees only pointers and L, T: the binding checks
+    shapes, dtypes, contiguity and the device first (CPU tensors here, so a
+    launch could not even start)."""
+    import torch
+    from paper_1512_03812_gb300 import binding
+    L, T = 6, 4
+    V = L * T
+    good = torch.zeros((V, 2), dtype=torch.complex128)
+    cases = [
+        (good, torch.zeros((V + 1, 2), dtype=torch.complex128), None, "psi must have shape"),
+        (torch.zeros((V, 2), dtype=torch.complex64), good, None, "U must have psi's dtype"),
+        (torch.zeros((V - 2, 2), dtype=torch.complex128), good, None, "U must have shape"),
+        (good, good, torch.zeros((V, 2), dtype=torch.complex64), "out must have psi's dtype"),
+        (good, torch.zeros((2, V), dtype=torch.complex128).t(), None, "psi must be contiguous"),
+        (good, torch.zeros((V, 2), dtype=torch.float64), None, "psi must be complex"),
+        (good, good, None, "must be on the current CUDA device"),
+    ]
+    for U, psi, out, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            binding.apply_DdagD_noalloc(L, T, 0.1, U, psi, out)

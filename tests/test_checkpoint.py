@@ -50,3 +50,21 @@ def test_refuses_foreign_truncated_and_mismatched(tmp_path):
     other = _lat()
     other.beta = np.array([2.0, 1.0])
     assert not ck.matches(ck.load(path), other)
+
+
+def test_failed_save_keeps_the_previous_checkpoint(tmp_path, monkeypatch):
+    lat = _lat()
+    path = tmp_path / "f.ckpt"
+    q0 = np.full((lat.N, 2), 0.25)
+    ck.save(path, lat, q0, 3)
+    before = path.read_bytes()
+
+    def full_disk(fd):
+        raise OSError(28, "No space left on device")
+
+    monkeypatch.setattr(ck.os, "fsync", full_disk)
+    with pytest.raises(OSError):
+        ck.save(path, lat, np.zeros((lat.N, 2)), 4)
+    assert path.read_bytes() == before
+    assert not (tmp_path / "f.ckpt.tmp").exists()
+    assert ck.load(path)["trajectory"] == 3
