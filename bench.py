@@ -91,11 +91,6 @@ NCU_CAPTURES = {
         "sources": {"paper_1512_03812_gb300/csrc/cg_chain.cu": "d3922942409cc196",
                     "paper_1512_03812_gb300/csrc/common.cuh": "078132e7c68d198a"},
         "dram_bytes_per_launch": 84524800 + 36106496},
-    "k_ddagd_stream": {
-        "sources": {"paper_1512_03812_gb300/csrc/stream.cuh": "8efeb63c67537b28",
-                    "paper_1512_03812_gb300/csrc/ddagd.cu": "37882365b98d9b4e",
-                    "paper_1512_03812_gb300/csrc/common.cuh": "2eb97b3f6b1ea47a"},
-        "dram_bytes_per_launch": 134622976 + 27326464},
 }
 
 
@@ -215,6 +210,119 @@ def aggregate(world, chains_per_rank, steps, ms_max):
     return world * chains_per_rank * steps / (ms_max / 1e3)
 
 
+def rank_env():
+    """(world size, rank, local rank) of this process (1, 0, 0 when not
+    started by torch.distributed.run)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _free_port():
+    import socket
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def rank_command(n, argv, port=None):
+    """The command that runs this script as n ranks on one node, one process
+    per GPU (torch.distributed.run, rendezvous on 127.0.0.1)."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+            f"--nproc-per-node={int(n)}", "--master-addr", "127.0.0.1",
+            "--master-port", str(port or _free_port()), os.path.abspath(__file__), *argv]
+
+
+def launch_ranks(n, argv, capture=False, timeout=None):
+    """Starts n ranks of this script with the arguments argv and waits for
+    them; returns the completed process (its stdout captured if asked)."""
+    return subprocess.run(rank_command(n, argv), capture_output=capture, text=True,
+                          timeout=timeout)
+
+
+def check_world(gpus, world):
+    """A run asked for `gpus` ranks must have been started as that many."""
+    if world != gpus:
+        raise SystemExit(f"bench.py: --gpus {gpus} but WORLD_SIZE is {world}; start it with "
+                         f"--gpus {gpus} alone (it launches its ranks) or under "
+                         f"torch.distributed.run --nproc-per-node {gpus}")
+
+
+def check_distinct(dist, key):
+    """Every rank reports a different `key` (its device): gathered on all
+    ranks, refused if two ranks share one."""
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return [key]
+    keys = [None] * dist.get_world_size()
+    dist.all_gather_object(keys, key)
+    if len(set(keys)) != len(keys):
+        raise SystemExit(f"bench.py: ranks share a device: {keys}")
+    return keys
+
+
+def run_rank_selftest(args):
+    """The rank logic of a multi-rank run without any GPU work (gloo on the
+    CPU): world size against --gpus, distinct local ranks, the shards and
+    seeds of the chains, and the max-over-ranks timing and the aggregate."""
+    import torch.distributed as dist
+    world, rank, local = rank_env()
+    check_world(args.gpus, world)
+    if world > 1:
+        dist.init_process_group("gloo")
+    locals_ = check_distinct(dist, local)
+    sh = shard(world, rank, args.chains)
+    shards = [None] * world
+    if world > 1:
+        dist.all_gather_object(shards, sh)
+    else:
+        shards = [sh]
+    ms = max_over_ranks(100.0 + 10.0 * rank, dist)
+    if rank == 0:
+        print(json.dumps({"world": world, "local_ranks": locals_, "shards": shards,
+                          "ms_max": ms, "value": aggregate(world, args.chains, 1, ms)}),
+              flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def bench_config(W, chains, world, args):
+    """The `config` of the JSON line, the same for both arms."""
+    return dict(W, chains_per_gpu=chains, precision=args.prec, parallelism=f"replicas{world}",
+                l2="flushed between steps (256 MiB write)", cuda_graph=bool(args.graph))
+
+
+def thermalise_64(P, dev, W, therm):
+    """One 64 x 64 configuration at the workload's couplings, thermalised by
+    this library's HMC (untimed): heavy fermions first (kappa 0.10: cheap,
+    stable), then the working kappa with small steps, every trajectory
+    accepted, then a few with Metropolis."""
+    import torch
+    L, T = W["L"], W["T"]
+    t0 = time.time()
+    q1 = torch.zeros((L * T, 2), dtype=torch.float64, device=dev)
+    g1 = torch.Generator(device=dev)
+    g1.manual_seed(99)
+    acc_th = []
+    fine = P.CG(1e-8, 20000, "mixed")
+    phases = [(0.10, P.MD(scheme="nested_leapfrog", tau=1.0, n=5, M=8, cg=fine), therm, 0.0),
+              (W["kappa"], P.MD(scheme="nested_leapfrog", tau=1.0, n=16, M=4, cg=fine),
+               therm // 2, 0.0),
+              (W["kappa"], P.MD(scheme="nested_leapfrog", tau=1.0, n=16, M=4, cg=fine),
+               therm // 4, None)]
+    for kap, mdt, ntraj, uforce in phases:
+        one = P.Lattice(L, T, W["beta"], kappa_to_m0(kap), device=dev)
+        for _ in range(ntraj):
+            p = torch.randn((L * T, 2), generator=g1, device=dev, dtype=torch.float64)
+            e = torch.view_as_complex(torch.randn((L * T, 2, 2), generator=g1, device=dev,
+                                                  dtype=torch.float64) * math.sqrt(0.5))
+            u = float(torch.rand(1, generator=g1, device=dev, dtype=torch.float64))
+            u = u if uforce is None else uforce
+            dH, _, acc = one.hmc_trajectory(q1, p, e.contiguous(), u, mdt, check=False)
+            acc_th.append((kap, bool(acc[0]), float(dH[0])))
+    log(f"thermalised in {time.time() - t0:.1f}s: " +
+        " ".join(f"k{k:.2f}:{'A' if a else 'r'}{d:+.2g}" for k, a, d in acc_th))
+    return q1
+
+
 # ------------------------------------------------------------ our arm ------
 
 def run_ours(args):
@@ -224,13 +332,16 @@ def run_ours(args):
     import paper_1512_03812_gb300 as P
     from paper_1512_03812_gb300 import binding
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
+    check_world(args.gpus, world)
+    if local >= torch.cuda.device_count():
+        raise SystemExit(f"bench.py: local rank {local} but {torch.cuda.device_count()} GPUs")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
+    props = torch.cuda.get_device_properties(dev)
+    check_distinct(dist, str(getattr(props, "uuid", local)))
     P.build()
 
     W = WORKLOAD
@@ -254,33 +365,7 @@ def run_ours(args):
         u = torch.rand((k, B), generator=gen, device=dev, dtype=torch.float64).cpu().numpy()
         return p, e, u
 
-    # thermalise one configuration, untimed: first with heavy fermions
-    # (kappa 0.10: cheap, stable), then at the working kappa with small steps
-    t0 = time.time()
-    q1 = torch.zeros((L * T, 2), dtype=torch.float64, device=dev)
-    g1 = torch.Generator(device=dev)
-    g1.manual_seed(99)
-    acc_th = []
-    # burn-in with forced acceptance (u = 0 accepts every finite Delta H),
-    # fine steps: heavy fermions first, then the working kappa
-    fine = P.CG(1e-8, 20000, "mixed")
-    phases = [(0.10, P.MD(scheme="nested_leapfrog", tau=1.0, n=5, M=8, cg=fine), args.therm, 0.0),
-              (W["kappa"], P.MD(scheme="nested_leapfrog", tau=1.0, n=16, M=4, cg=fine),
-               args.therm // 2, 0.0),
-              (W["kappa"], P.MD(scheme="nested_leapfrog", tau=1.0, n=16, M=4, cg=fine),
-               args.therm // 4, None)]
-    for kap, mdt, ntraj, uforce in phases:
-        one = P.Lattice(L, T, W["beta"], kappa_to_m0(kap), device=dev)
-        for _ in range(ntraj):
-            p = torch.randn((L * T, 2), generator=g1, device=dev, dtype=torch.float64)
-            e = torch.view_as_complex(torch.randn((L * T, 2, 2), generator=g1, device=dev,
-                                                  dtype=torch.float64) * math.sqrt(0.5))
-            u = float(torch.rand(1, generator=g1, device=dev, dtype=torch.float64))
-            u = u if uforce is None else uforce
-            dH, _, acc = one.hmc_trajectory(q1, p, e.contiguous(), u, mdt, check=False)
-            acc_th.append((kap, bool(acc[0]), float(dH[0])))
-    log(f"thermalised in {time.time() - t0:.1f}s: " +
-        " ".join(f"k{k:.2f}:{'A' if a else 'r'}{d:+.2g}" for k, a, d in acc_th))
+    q1 = thermalise_64(P, dev, W, args.therm)
     q_start = q1.repeat(B, 1).contiguous()
 
     flush = torch.empty(int(256 * 2 ** 20), dtype=torch.uint8, device=dev)
@@ -388,57 +473,98 @@ def run_ours(args):
     d2h = int(B * (8 + 8 + 4))
 
     # FP64 path on the same inputs: Delta H deviation and throughput
-    fp64 = None
-    if args.fp64_steps > 0:
-        md64 = P.MD(scheme=W["scheme"], tau=W["tau"], n=W["n"], M=W["M"], fg=W["fg"],
-                    cg=P.CG(tol=W["cg_tol"], maxit=20000, prec="f64", algo=args.algo),
-                    tol_action=W["cg_tol_action"], sf_start=args.sf_start)
-        q64 = q_start.clone()
-        qm = q_start.clone()
-        dev_max = 0.0
-        acc64, accm = [], []
-        torch.cuda.synchronize()
+    def md_with(prec, tol, algo=None, variant=None):
+        return P.MD(scheme=W["scheme"], tau=W["tau"], n=W["n"], M=W["M"], fg=W["fg"],
+                    cg=P.CG(tol=tol, maxit=50000, prec=prec, algo=algo or args.algo,
+                            delta=args.delta),
+                    tol_action=min(tol, W["cg_tol_action"]), sf_start=args.sf_start)
+
+    def compare(md_a, md_b, steps, time_a=True, time_b=True, lat_b=None):
+        """Both arms from q_start on the same momenta, noise and uniforms,
+        `steps` trajectories each (the chains of arm b are reset to arm a's
+        after every trajectory, so both take the same path); per arm the
+        event-timed trajectories/s (flushed L2, as in the timed steps)."""
+        lb = lat_b or lat
+        qa, qb = q_start.clone(), q_start.clone()
+        dev_max, same, ta, tb, acc_a, acc_b = 0.0, [], 0.0, 0.0, [], []
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
-        t64 = 0.0
-        for i in range(args.fp64_steps):
+        for i in range(steps):
             flush.fill_(1)
             f0.record()
-            d64, _, a64 = lat.hmc_trajectory(q64, pk[i], ek[i], uk[i], md64, check=False)
+            da, _, aa = lat.hmc_trajectory(qa, pk[i], ek[i], uk[i], md_a, check=False)
             f1.record()
             torch.cuda.synchronize()
-            t64 += f0.elapsed_time(f1)
-            dm, _, am = lat.hmc_trajectory(qm, pk[i], ek[i], uk[i], md, check=False)
-            accm.append(am)
-            ok = np.isfinite(d64) & np.isfinite(dm)
-            dev_max = max(dev_max, float(np.abs(d64[ok] - dm[ok]).max()) if ok.any() else 0.0)
-            acc64.append(a64)
-            qm.copy_(q64)
-        same = float(np.mean(np.concatenate(acc64) == np.concatenate(accm)))
-        fp64 = {"traj_per_s": world * B * args.fp64_steps / (t64 / 1e3),
-                "acc": float(np.mean(np.concatenate(acc64))),
-                "acc_mixed_same_inputs": float(np.mean(np.concatenate(accm))),
-                "same_decisions": same,
-                "max_abs_dH_mixed_minus_fp64": dev_max, "steps": args.fp64_steps,
-                "cg_tol": W["cg_tol"]}
-        if args.tight_tol > 0:
-            # the same comparison with both paths solving to a tighter true
-            # residual: the deviation follows the tolerance, not FP32 arithmetic
-            def md_at(prec):
-                return P.MD(scheme=W["scheme"], tau=W["tau"], n=W["n"], M=W["M"], fg=W["fg"],
-                            cg=P.CG(tol=args.tight_tol, maxit=50000, prec=prec, algo=args.algo,
-                                    delta=args.delta),
-                            tol_action=min(args.tight_tol, W["cg_tol_action"]),
-                            sf_start=args.sf_start)
-            qa, qb = q_start.clone(), q_start.clone()
-            da, _, aa = lat.hmc_trajectory(qa, pk[0], ek[0], uk[0], md_at("f64"), check=False)
-            db, _, ab = lat.hmc_trajectory(qb, pk[0], ek[0], uk[0], md_at("mixed"), check=False)
+            ta += f0.elapsed_time(f1)
+            flush.fill_(1)
+            f0.record()
+            db, _, ab = lb.hmc_trajectory(qb, pk[i], ek[i], uk[i], md_b, check=False)
+            f1.record()
+            torch.cuda.synchronize()
+            tb += f0.elapsed_time(f1)
             ok = np.isfinite(da) & np.isfinite(db)
-            fp64["tight_tol"] = {"cg_tol": args.tight_tol,
-                                 "max_abs_dH_mixed_minus_fp64":
-                                     float(np.abs(da[ok] - db[ok]).max()) if ok.any() else None,
-                                 "same_decisions": float(np.mean(aa == ab)), "trajectories": B}
-            del qa, qb
+            if ok.any():
+                dev_max = max(dev_max, float(np.abs(da[ok] - db[ok]).max()))
+            same.append(aa == ab)
+            acc_a.append(aa)
+            acc_b.append(ab)
+            qb.copy_(qa)
+        n = world * B * steps
+        return {"traj_per_s_a": n / (ta / 1e3) if time_a else None,
+                "traj_per_s_b": n / (tb / 1e3) if time_b else None,
+                "max_abs_dH_diff": dev_max,
+                "same_decisions": float(np.mean(np.concatenate(same))),
+                "acc_a": float(np.mean(np.concatenate(acc_a))),
+                "acc_b": float(np.mean(np.concatenate(acc_b))), "steps": steps,
+                "trajectories_per_arm": n}
+
+    fp64 = None
+    if args.fp64_steps > 0:
+        # at the workload's tolerance: FP64 (a) against mixed (b)
+        r = compare(md_with("f64", W["cg_tol"]), md, args.fp64_steps)
+        fp64 = {"traj_per_s": r["traj_per_s_a"], "traj_per_s_mixed_same_inputs": r["traj_per_s_b"],
+                "acc": r["acc_a"], "acc_mixed_same_inputs": r["acc_b"],
+                "same_decisions": r["same_decisions"],
+                "max_abs_dH_mixed_minus_fp64": r["max_abs_dH_diff"], "steps": args.fp64_steps,
+                "cg_tol": W["cg_tol"]}
+        log(f"fp64 at {W['cg_tol']}: {r}")
+        # the deviation any two correct solvers show at this tolerance: FP64
+        # chain-resident against FP64 grid-wide (other reduction order, other
+        # iterates), and two kernel variants of the mixed solver
+        r = compare(md_with("f64", W["cg_tol"], algo="chain"), md_with("f64", W["cg_tol"], algo="grid"),
+                    1, time_a=False, time_b=False)
+        fp64["floor_f64_chain_vs_f64_grid"] = {"cg_tol": W["cg_tol"],
+                                               "max_abs_dH_diff": r["max_abs_dH_diff"],
+                                               "same_decisions": r["same_decisions"],
+                                               "trajectories": r["trajectories_per_arm"]}
+        log(f"floor f64 chain vs grid: {r}")
+        if tune and not tune.get("pinned"):
+            alt = 2 if tune["variant"] != 2 else 1
+            lat2 = P.Lattice([L] * B, [T] * B, W["beta"], m0, device=dev)
+            lat2.set_cg_variant(alt)
+            r = compare(md, md, 1, time_a=False, time_b=False, lat_b=lat2)
+            fp64["floor_mixed_variant_%d_vs_%d" % (tune["variant"], alt)] = {
+                "cg_tol": W["cg_tol"], "max_abs_dH_diff": r["max_abs_dH_diff"],
+                "same_decisions": r["same_decisions"], "trajectories": r["trajectories_per_arm"]}
+            log(f"floor mixed variants: {r}")
+            del lat2
+    if args.tight_tol > 0 and args.tight_steps > 0:
+        # both paths timed at the tolerance at which their Delta H agree
+        # within 1e-8: FP64 (a) against mixed (b), MD and action solves at
+        # tight_tol
+        r = compare(md_with("f64", args.tight_tol), md_with("mixed", args.tight_tol),
+                    args.tight_steps)
+        tight = {"cg_tol": args.tight_tol, "cg_tol_action": min(args.tight_tol, W["cg_tol_action"]),
+                 "traj_per_s_fp64": r["traj_per_s_a"], "traj_per_s_mixed": r["traj_per_s_b"],
+                 "mixed_over_fp64": r["traj_per_s_b"] / r["traj_per_s_a"],
+                 "max_abs_dH_mixed_minus_fp64": r["max_abs_dH_diff"],
+                 "same_decisions": r["same_decisions"], "acc_fp64": r["acc_a"],
+                 "acc_mixed": r["acc_b"], "steps": r["steps"],
+                 "trajectories_per_arm": r["trajectories_per_arm"],
+                 "target_dH_within": 1e-8,
+                 "meets_target": bool(r["max_abs_dH_diff"] <= 1e-8 and r["same_decisions"] == 1.0)}
+        log(f"tight tol {args.tight_tol}: {tight}")
+        fp64 = dict(fp64 or {}, tight_tol=tight)
 
     # roofline of the dominant kernel: the CG solve.  The chain-resident form
     # (every chain of this workload fits) keeps U, p, t in shared memory and
@@ -485,16 +611,23 @@ def run_ours(args):
                  "f64": measure_ddagd(torch, P, dev, prec="f64", rates=rates)}
     if rank != 0:
         return
-    cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu) else None
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        # the oracle on the host cores, from the same thermalised start with
+        # the first timed step's momenta, noise and uniforms
+        qh = q_start[:L * T].cpu().numpy()
+        ph, eh = pk[0].cpu().numpy(), ek[0].cpu().numpy()
+        jobs = [(qh, ph[c * L * T:(c + 1) * L * T], eh[c * L * T:(c + 1) * L * T], float(uk[0][c]))
+                for c in range(B)]
+        cpu = cpu_baseline(jobs)
     out = {
         "metric": "HMC trajectories/s", "value": round(traj_per_s, 3),
         "unit": "trajectories/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": round(ms_max / K, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.prec == "mixed" else "f64",
         "data": "synthetic (own thermalised start, seeded momenta/noise)",
-        "config": dict(W, chains_per_gpu=B, precision=args.prec, parallelism=f"replicas{world}",
-                       l2="flushed between steps (256 MiB write)", cg_autotune=tune,
-                       cuda_graph=bool(args.graph)),
+        "config": bench_config(W, B, world, args),
+        "cg_autotune": tune,
         "acceptance": round(acc_rate, 4),
         "e2e": {"value": round(aggregate(world, B, K, e2e_ms), 3), "unit": "trajectories/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -692,6 +825,125 @@ def run_other(args):
         "clocks": clk}), flush=True)
 
 
+# ------------------------- mixed against FP64 over step sizes (64 x 64) ------
+
+SWEEP = {
+    "workload": "64x64 beta=2.0 kappa=0.26, 200 momentum sets from one thermalised "
+                "configuration per point, tau=1, outer n in {4,6,8,10}, inner m in {1,2,4} "
+                "(nested schemes), mixed CG (FP32 + FP64 reliable updates) against FP64 CG, "
+                "tol 1e-10 (1e-12 for the S_F of H)",
+    "chains": 200, "n": (4, 6, 8, 10), "M": (1, 2, 4),
+    "schemes": [("leapfrog", None), ("five_stage", "2mn"), ("five_stage_fg", None),
+                ("nested_leapfrog", None), ("nested_fg", None), ("adapted_nested_fg", None)],
+}
+
+
+def _slope(hs, ys):
+    """Least-squares slope of log y against log h (the order of Delta H in h)."""
+    ok = [(h, y) for h, y in zip(hs, ys) if y and y > 0 and math.isfinite(y)]
+    if len(ok) < 2:
+        return None
+    x = np.log([h for h, _ in ok])
+    y = np.log([v for _, v in ok])
+    return float(np.polyfit(x, y, 1)[0])
+
+
+def run_sweep(args):
+    """The mixed-precision against FP64 configuration over step sizes: for
+    every scheme, outer n and (nested schemes) inner m, one batch of 200
+    chains from the same thermalised configuration with fresh momenta and
+    noise, once with the mixed CG and once with the FP64 CG on the same
+    inputs: acceptance, <|Delta H|>, max |Delta H_mixed - Delta H_FP64| and
+    the decisions; then the slope of <|Delta H|> against h per scheme and m
+    for both paths.  Writes the JSON to --out as well as to stdout."""
+    import torch
+
+    import paper_1512_03812_gb300 as P
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    P.build()
+    W = dict(WORKLOAD)
+    L, T, B = W["L"], W["T"], SWEEP["chains"]
+    q1 = thermalise_64(P, dev, W, args.therm)
+    lat = P.Lattice([L] * B, [T] * B, W["beta"], kappa_to_m0(W["kappa"]), device=dev)
+    N = lat.N
+    qb = q1.repeat(B, 1).contiguous()
+    g = torch.Generator(device=dev)
+    g.manual_seed(2604)
+    cg_m = P.CG(tol=W["cg_tol"], maxit=50000, prec="mixed", delta=args.delta)
+    cg_d = P.CG(tol=W["cg_tol"], maxit=50000, prec="f64")
+    rows = []
+    t_m = t_d = 0.0
+    t0 = time.time()
+    for scheme, variant in SWEEP["schemes"]:
+        Ms = SWEEP["M"] if "nested" in scheme else (1,)
+        lam = P.LAMBDA_2MN if variant == "2mn" else 1.0 / 6.0
+        for M in Ms:
+            for n in SWEEP["n"]:
+                p = torch.randn((N, 2), generator=g, device=dev, dtype=torch.float64)
+                e = torch.view_as_complex(torch.randn((N, 2, 2), generator=g, device=dev,
+                                                      dtype=torch.float64) * math.sqrt(0.5))
+                e = e.contiguous()
+                u = torch.rand(B, generator=g, device=dev, dtype=torch.float64).cpu().numpy()
+                out = {}
+                for name, cg in (("mixed", cg_m), ("fp64", cg_d)):
+                    md = P.MD(scheme=scheme, tau=W["tau"], n=n, M=M, lam=lam, fg=W["fg"], cg=cg,
+                              tol_action=W["cg_tol_action"])
+                    q = qb.clone()
+                    torch.cuda.synchronize()
+                    ta = time.time()
+                    dH, _, acc = lat.hmc_trajectory(q, p, e, u, md, check=False)
+                    dt = time.time() - ta
+                    if name == "mixed":
+                        t_m += dt
+                    else:
+                        t_d += dt
+                    out[name] = (dH, acc, dt)
+                dm, am, _ = out["mixed"]
+                dd, ad, _ = out["fp64"]
+                ok = np.isfinite(dm) & np.isfinite(dd)
+                row = {"scheme": scheme + ("_2mn" if variant == "2mn" else ""), "n": n,
+                       "h": W["tau"] / n, "M": M if "nested" in scheme else None}
+                for name, (dH, acc, dt) in out.items():
+                    f = np.isfinite(dH)
+                    row[name] = {"acceptance": float(np.mean(acc)),
+                                 "mean_abs_dH": float(np.abs(dH[f]).mean()) if f.any() else None,
+                                 "median_abs_dH": float(np.median(np.abs(dH[f]))) if f.any() else None,
+                                 "nonfinite": int((~f).sum()), "seconds": round(dt, 3)}
+                row["max_abs_dH_mixed_minus_fp64"] = (float(np.abs(dm[ok] - dd[ok]).max())
+                                                      if ok.any() else None)
+                row["same_decisions"] = float(np.mean(am == ad))
+                rows.append(row)
+                log(f"sweep {row['scheme']} n={n} M={M}: acc {row['mixed']['acceptance']:.3f}/"
+                    f"{row['fp64']['acceptance']:.3f} dev {row['max_abs_dH_mixed_minus_fp64']:.2e}")
+    slopes = []
+    keys = sorted({(r["scheme"], r["M"]) for r in rows}, key=str)
+    for sch, M in keys:
+        rs = [r for r in rows if r["scheme"] == sch and r["M"] == M]
+        hs = [r["h"] for r in rs]
+        slopes.append({"scheme": sch, "M": M,
+                       "slope_mixed": _slope(hs, [r["mixed"]["median_abs_dH"] for r in rs]),
+                       "slope_fp64": _slope(hs, [r["fp64"]["median_abs_dH"] for r in rs])})
+    devs = [r["max_abs_dH_mixed_minus_fp64"] for r in rows
+            if r["max_abs_dH_mixed_minus_fp64"] is not None]
+    res = {"metric": "mixed against FP64 over step sizes", "workload": SWEEP["workload"],
+           "data": "synthetic (own thermalised start, seeded momenta/noise)",
+           "chains": B, "cg_tol": W["cg_tol"], "cg_tol_action": W["cg_tol_action"],
+           "cg_delta": args.delta,
+           "trajectories_per_path": B * len(rows),
+           "wall_s": {"mixed": round(t_m, 2), "fp64": round(t_d, 2),
+                      "fp64_over_mixed": round(t_d / t_m, 2) if t_m else None,
+                      "total": round(time.time() - t0, 1)},
+           "max_abs_dH_mixed_minus_fp64_overall": max(devs) if devs else None,
+           "same_decisions_overall": float(np.mean([r["same_decisions"] for r in rows])),
+           "slope_of_median_abs_dH_in_h": slopes, "points": rows}
+    line = json.dumps(res)
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(json.dumps(res, indent=1) + "\n")
+    print(line, flush=True)
+
+
 # ------------------------------------- the paper's own numerical experiment --
 
 # Sec. 5 of the paper: a 32 x 32 lattice, beta = 1.0, m0 = -0.231367, one
@@ -791,6 +1043,65 @@ def run_paper(args):
                 "mean_abs_dH_all": float(a.mean()),
                 "inversions_per_traj_md": int(st["inversions"])}
 
+    def measure_n(scheme, fg, n, draws):
+        """Acceptance and inversions at n steps on fixed draws (the same
+        momenta and noise for every n of one integrator)."""
+        md = P.MD(scheme=scheme, tau=Wp["tau"], n=n, M=Wp["M"], fg=fg, cg=cg, tol_action=1e-12,
+                  merge_kicks=False)
+        p, e, u = draws
+        q = qb.clone()
+        dH, _, acc = lat.hmc_trajectory(q, p, e, u, md, check=False)
+        st = lat.stats.as_dict()
+        ok = np.isfinite(dH)
+        return {"n": n, "h": round(Wp["tau"] / n, 6), "acceptance": float(np.mean(acc)),
+                "acceptance_expected": float(np.mean(np.exp(np.minimum(0.0, -dH[ok]))) * ok.mean()),
+                "inversions_per_traj_md": int(st["inversions"])}
+
+    def h_at_90(scheme, fg, h_paper):
+        """The step size at 90 % acceptance: the smallest n = tau / h whose
+        expected acceptance <min(1, e^-dH)> over the 200 momentum sets is at
+        least 0.9, found by bracketing from the paper's h and bisecting over
+        integer n on one fixed set of draws; h90 interpolated linearly in h
+        between the bracketing n."""
+        draws = draw(B, B * L * T)
+        seen = {}
+
+        def A(n):
+            if n not in seen:
+                seen[n] = measure_n(scheme, fg, n, draws)
+            return seen[n]["acceptance_expected"]
+
+        n0 = max(2, int(math.ceil(Wp["tau"] / h_paper - 1e-9)))
+        if A(n0) >= 0.9:
+            hi, lo = n0, max(1, n0 // 2)
+            while lo > 1 and A(lo) >= 0.9:
+                hi, lo = lo, max(1, lo // 2)
+            if A(lo) >= 0.9:
+                hi = lo
+        else:
+            lo, hi = n0, 2 * n0
+            while A(hi) < 0.9 and hi < 4096:
+                lo, hi = hi, 2 * hi
+        while hi - lo > 1:
+            mid = (lo + hi) // 2
+            if A(mid) >= 0.9:
+                hi = mid
+            else:
+                lo = mid
+        a_hi, h_hi = A(hi), Wp["tau"] / hi
+        h90 = h_hi
+        if lo != hi:
+            a_lo, h_lo = A(lo), Wp["tau"] / lo
+            if a_lo < 0.9 <= a_hi and a_hi > a_lo:
+                h90 = h_lo + (0.9 - a_lo) * (h_hi - h_lo) / (a_hi - a_lo)
+        r = seen[hi]
+        return {"h90": round(h90, 5), "n": hi, "h_at_n": round(h_hi, 6),
+                "acceptance_expected_at_n": round(a_hi, 4),
+                "acceptance_at_n": round(r["acceptance"], 4),
+                "inversions_per_traj_md_at_n": r["inversions_per_traj_md"],
+                "evaluated": sorted(({"n": k, "acceptance_expected": round(v["acceptance_expected"], 4)}
+                                     for k, v in seen.items()), key=lambda d: d["n"])}
+
     t1 = time.time()
     table = []
     for scheme, fg, h, per_step, per_traj in Wp["table1"]:
@@ -800,6 +1111,9 @@ def run_paper(args):
         r["inversions_per_traj_md_merged_kicks"] = measure(scheme, fg, h)["inversions_per_traj_md"]
         r.update({"paper_h": h, "paper_inversions_per_step": per_step,
                   "paper_inversions_per_traj": per_traj})
+        if not args.no_h90:
+            r["at_90_percent"] = h_at_90(scheme, fg, h)
+            log(f"paper h90 {scheme}/{fg}: {r['at_90_percent']}")
         table.append(r)
         log(f"paper table1 {scheme}/{fg} h={r['h']}: acc {r['acceptance']} median |dH| "
             f"{r['median_abs_dH']:.4g} unstable {r['unstable']} inversions "
@@ -809,8 +1123,9 @@ def run_paper(args):
         for h in Wp["scan_h"]:
             scan.append(measure(scheme, fg, h))
     dt = time.time() - t1
-    ntraj = B * (len(table) + len(scan))
-    print(json.dumps({
+    ntraj = B * (len(table) + len(scan) + sum(len(r.get("at_90_percent", {}).get("evaluated", []))
+                                             for r in table))
+    res = {
         "metric": "paper workload: trajectories/s over the Table 1 and Fig. 1 runs",
         "value": round(ntraj / dt, 3), "unit": "trajectories/s", "n_gpus": 1,
         "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic (own thermalised start)",
@@ -824,7 +1139,11 @@ def run_paper(args):
         "inversions_counting": "D^-1 per trajectory in the MD (one D^dag D solve = 2; the "
                                "two solves of H are not counted); Table 1 rows with every kick "
                                "evaluated (as the paper counts), plus the merged-kick count",
-        "table1": table, "scan": scan}), flush=True)
+        "table1": table, "scan": scan}
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(json.dumps(res, indent=1) + "\n")
+    print(json.dumps(res), flush=True)
 
 
 # ------------------------------------------------- D^dag D at 2048 x 2048 --
@@ -833,30 +1152,53 @@ DDAGD_FLOPS_PER_SITE = 112  # two stages of 4 hops x 11 flops + 12 for the diago
 
 
 def measure_ddagd(torch, P, dev, reps=20, prec="f32", warmup=3, rates=None):
-    """Fused D^dag D (sm_apply_DdagD) on one 2048 x 2048 lattice: CUDA-event
-    time per launch with L2 flushed before each launch; algorithmic bytes
-    48 (FP32) or 96 (FP64) per site: read in and U once, write out once."""
+    """Fused D^dag D (sm_apply_DdagD) on one 2048 x 2048 lattice; algorithmic
+    bytes 48 (FP32) or 96 (FP64) per site: read in and U once, write out once.
+
+    The headline figure times `reps` launches back to back inside one event
+    pair, alternating between two independent sets of (U, in, out), so that
+    no launch finds its operands in L2 and each pays for the write-back of
+    its predecessor's output: in steady state a launch's DRAM traffic is its
+    algorithmic bytes.  The single-launch figure (L2 flushed and clean before
+    each launch, one event pair per launch) is kept beside it: it does not
+    pay for its own output still dirty in L2 when the kernel ends."""
     L = T = 2048
     lat = P.Lattice(L, T, 8.0, kappa_to_m0(0.255), device=dev)
     g = torch.Generator(device=dev)
     g.manual_seed(5)
-    q = (torch.rand((L * T, 2), generator=g, device=dev, dtype=torch.float64) * 2 - 1) * math.pi
-    U64, U32 = lat.links(q)
     cdt = torch.complex64 if prec == "f32" else torch.complex128
-    psi = torch.randn((L * T, 2), generator=g, device=dev, dtype=cdt)
-    out = torch.empty_like(psi)
-    U = U32 if prec == "f32" else U64
+    sets = []
+    for _ in range(2):
+        q = (torch.rand((L * T, 2), generator=g, device=dev, dtype=torch.float64) * 2 - 1) * math.pi
+        U64, U32 = lat.links(q)
+        psi = torch.randn((L * T, 2), generator=g, device=dev, dtype=cdt)
+        sets.append((U32 if prec == "f32" else U64, psi, torch.empty_like(psi)))
+        del q
     # L2 flush: write 256 MiB (evicts the operands), then read another 256
     # MiB, so that the flush's own dirty lines are written back before the
     # timed launch instead of inside it
     flush = torch.empty(int(256 * 2 ** 20), dtype=torch.uint8, device=dev)
     clean = torch.zeros(int(32 * 2 ** 20), dtype=torch.int64, device=dev)
-    for _ in range(warmup):
+    for i in range(warmup):
+        U, psi, out = sets[i % 2]
         lat.apply_DdagD(U, psi, out)
-    ts = []
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    for _ in range(reps):
+    # back to back, from a clean L2
+    flush.fill_(2)
+    clean.sum()
+    torch.cuda.synchronize()
+    e0.record()
+    for i in range(reps):
+        U, psi, out = sets[i % 2]
+        lat.apply_DdagD(U, psi, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_b2b = e0.elapsed_time(e1) / reps
+    # one launch per event pair
+    ts = []
+    for i in range(reps):
+        U, psi, out = sets[i % 2]
         flush.fill_(2)
         clean.sum()
         e0.record()
@@ -866,16 +1208,26 @@ def measure_ddagd(torch, P, dev, reps=20, prec="f32", warmup=3, rates=None):
         ts.append(e0.elapsed_time(e1))
     ms = float(np.median(ts))
     bps = 48 if prec == "f32" else 96
-    gbs = bps * L * T / (ms / 1e3) / 1e9
+    gbs = bps * L * T / (ms_b2b / 1e3) / 1e9
+    gbs1 = bps * L * T / (ms / 1e3) / 1e9
     peaks, src = measured_peaks()
-    return {"kernel": "k_ddagd_stream" if prec == "f32" else "k_ddagd_tile<double>",
-            "lattice": "2048x2048",
-            "ms_median": round(ms, 4), "bytes_per_site": bps, "achieved": round(gbs, 1),
-            "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-            "frac": round(gbs / float(peaks["hbm_gbs"]), 4), "peak_source": src,
-            "l2": "flushed before each launch (write 256 MiB, then read 256 MiB)", "reps": reps,
-            "traffic": ncu_traffic("k_ddagd_stream") if prec == "f32" else None,
-            **fp64_roofline(ms, L * T, prec, rates)}
+    hbm = float(peaks["hbm_gbs"])
+    kname = "k_ddagd_stream" if prec == "f32" else "k_ddagd_tile<double>"
+    return {"kernel": kname, "lattice": "2048x2048",
+            "ms_per_launch": round(ms_b2b, 4), "bytes_per_site": bps,
+            "algorithmic_bytes_per_launch": bps * L * T, "achieved": round(gbs, 1),
+            "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4), "peak_source": src,
+            "timing": f"{reps} launches back to back in one event pair, two alternating operand "
+                      "sets (402 MB), L2 clean at the start",
+            "single_launch": {"ms_median": round(ms, 4), "achieved": round(gbs1, 1),
+                              "frac": round(gbs1 / hbm, 4),
+                              "l2": "flushed and clean before each launch (write 256 MiB, then "
+                                    "read 256 MiB); the launch's own dirty output is written "
+                                    "back after its end event"},
+            "reps": reps, "traffic": ncu_traffic(kname) if prec == "f32" else None,
+            "traffic_unit": "DRAM bytes per launch (ncu, back-to-back launches, cache control "
+                            "none)",
+            **fp64_roofline(ms_b2b, L * T, prec, rates)}
 
 
 def fp64_roofline(ms, sites, prec, rates):
@@ -893,45 +1245,137 @@ def fp64_roofline(ms, sites, prec, rates):
 
 # ------------------------------------------------------- oracle (CPU) ------
 
-def oracle_sample(seed=0):
-    """One trajectory of one chain of the workload with the FP64 oracle;
-    returns seconds."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _oracle_trajectory(job):
+    """One HMC trajectory of one 64 x 64 chain of the workload with the FP64
+    oracle (a worker of the CPU baseline); job = (q, p, eta, u) of the chain,
+    host arrays in the site-major layout.  Returns its seconds."""
+    from oracle import integrators as ig
+    from oracle import schwinger as sw
+    W = WORKLOAD
+    L, T = W["L"], W["T"]
+    q, p, eta, u = job
+    lat = sw.Lattice(L, T, W["beta"], kappa_to_m0(W["kappa"]))
+    t0 = time.time()
+    ig.hmc_trajectory(lat, q.reshape(T, L, 2), p.reshape(T, L, 2), eta.reshape(T, L, 2), u,
+                      W["scheme"], W["tau"], W["n"], M=W["M"], fg=W["fg"],
+                      solver=sw.Solver(tol=W["cg_tol"]))
+    return time.time() - t0
+
+
+def _noop(x):
+    return x
+
+
+class OraclePool:
+    """A process pool of single-threaded oracle workers, one per host core,
+    started with `spawn` (a forked copy of a process that holds a CUDA
+    context can hang)."""
+
+    def __init__(self, cores):
+        import multiprocessing as mp
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[v] = "1"  # inherited by the workers: one thread each
+        self.cores = cores
+        self.pool = mp.get_context("spawn").Pool(cores)
+        self.pool.map(_noop, range(cores))  # workers up before any timing
+
+    def run(self, jobs):
+        """Runs the jobs; returns (wall seconds, per-job seconds)."""
+        t0 = time.time()
+        ts = self.pool.map(_oracle_trajectory, jobs, chunksize=1)
+        return time.time() - t0, ts
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(jobs):
+    """The oracle timed on the host cores: one trajectory of each of the
+    first `cores` chains in parallel (one single-threaded worker per core),
+    and one trajectory alone on one core (the 1-thread figure)."""
+    cores = min(host_cores(), len(jobs))
+    t1 = _oracle_trajectory(jobs[0])
+    pool = OraclePool(cores)
+    try:
+        wall, ts = pool.run(jobs[:cores])
+    finally:
+        pool.close()
+    return {"value": round(cores / wall, 5), "unit": "trajectories/s", "cores": cores,
+            "host_cores": host_cores(), "kind": "oracle",
+            "single_thread": {"value": round(1.0 / t1, 5), "cores": 1, "seconds": round(t1, 2)},
+            "sample": f"1 trajectory of each of {cores} chains (64x64, the GPU arm's thermalised "
+                      f"start and its first timed step's momenta, noise and uniforms), one "
+                      f"single-threaded numpy FP64 worker per core, {wall:.1f}s wall "
+                      f"(mean {np.mean(ts):.1f}s per trajectory)"}
+
+
+def oracle_start(seed=99, ntraj=20):
+    """A start configuration for the reference arm thermalised by the oracle
+    alone: the first phase of the GPU arm's thermalisation (heavy fermions,
+    kappa = 0.10, nested leapfrog n = 5, M = 8, every trajectory accepted),
+    cheap on the host because its solves converge in a few dozen
+    iterations."""
     from oracle import integrators as ig
     from oracle import schwinger as sw
     from paper_1512_03812_gb300 import inputs as I
     W = WORKLOAD
     L, T = W["L"], W["T"]
-    lat = sw.Lattice(L, T, W["beta"], kappa_to_m0(W["kappa"]))
+    lat = sw.Lattice(L, T, W["beta"], kappa_to_m0(0.10))
     q = np.zeros((T, L, 2))
-    p = I.momenta(L, T, seed).reshape(T, L, 2)
-    eta = I.noise(L, T, seed + 1).reshape(T, L, 2)
-    t0 = time.time()
-    ig.hmc_trajectory(lat, q, p, eta, 0.5, W["scheme"], W["tau"], W["n"], M=W["M"], fg=W["fg"],
-                      solver=sw.Solver(tol=W["cg_tol"]))
-    return time.time() - t0
-
-
-def cpu_baseline(args):
-    dt = oracle_sample()
-    return {"value": round(1.0 / dt, 5), "unit": "trajectories/s", "cores": 1, "kind": "oracle",
-            "sample": "1 trajectory of 1 chain (64x64, cold start, same scheme and CG tolerance), "
-                      f"numpy FP64 single thread, {dt:.1f}s"}
+    for k in range(ntraj):
+        r = ig.hmc_trajectory(lat, q, I.momenta(L, T, seed + 2 * k).reshape(T, L, 2),
+                              I.noise(L, T, seed + 2 * k + 1).reshape(T, L, 2), 0.0,
+                              "nested_leapfrog", 1.0, 5, M=8, solver=sw.Solver(tol=1e-8))
+        q = r.q_md
+    return q.reshape(L * T, 2)
 
 
 def run_reference(args):
-    if int(os.environ.get("RANK", "0")) != 0:
+    """The oracle as the reference arm: each step one trajectory of each of
+    `cores` chains in parallel on the host cores (a bounded sample of the
+    workload; rank 0 only)."""
+    world, rank, _ = rank_env()
+    if rank != 0:
         return
-    for _ in range(args.warmup):
-        oracle_sample(seed=100)
-    ts = [oracle_sample(seed=200 + i) for i in range(args.steps)]
-    v = len(ts) / sum(ts)
+    from paper_1512_03812_gb300 import inputs as I
+    W = WORKLOAD
+    L, T = W["L"], W["T"]
+    t0 = time.time()
+    q = oracle_start()
+    log(f"reference: oracle start thermalised in {time.time() - t0:.1f}s")
+    cores = host_cores()
+    pool = OraclePool(cores)
+
+    def jobs(step):
+        s = 1000 + 97 * step
+        return [(q, I.momenta(L, T, s + 3 * c), I.noise(L, T, s + 3 * c + 1),
+                 float(I.uniforms(1, s + 3 * c + 2)[0])) for c in range(cores)]
+
+    try:
+        for i in range(args.warmup):
+            pool.run(jobs(i))
+        walls = [pool.run(jobs(args.warmup + i))[0] for i in range(args.steps)]
+    finally:
+        pool.close()
+    v = args.steps * cores / sum(walls)
+    sample = (f"per step 1 trajectory of each of {cores} chains in parallel, one single-threaded "
+              f"numpy FP64 worker per host core; start thermalised by the oracle (kappa 0.10)")
     print(json.dumps({
         "impl": "reference", "metric": "HMC trajectories/s", "value": round(v, 5),
         "unit": "trajectories/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(1e3 * sum(ts) / len(ts), 1), "higher_is_better": True,
-        "config": WORKLOAD, "dtype": "f64", "data": "synthetic",
-        "cpu_baseline": {"value": round(v, 5), "kind": "oracle", "cores": 1,
-                         "sample": "per step 1 trajectory of 1 chain, numpy FP64 single thread"},
+        "ms_per_step": round(1e3 * sum(walls) / len(walls), 1), "higher_is_better": True,
+        "scaling": "weak", "config": bench_config(W, args.chains, world, args), "dtype": "f64",
+        "data": "synthetic (oracle-thermalised start, seeded momenta/noise)",
+        "cpu_baseline": {"value": round(v, 5), "unit": "trajectories/s", "kind": "oracle",
+                         "cores": cores, "sample": sample},
         "e2e": {"value": round(v, 5), "unit": "trajectories/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}), flush=True)
 
@@ -952,16 +1396,16 @@ def run_stencil(args):
                         rates=rates)
     print(json.dumps({"metric": "fused D^dag D stencil, algorithmic GB/s", "value": f32["achieved"],
                       "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-                      "ms_per_step": f32["ms_median"], "higher_is_better": True,
+                      "ms_per_step": f32["ms_per_launch"], "higher_is_better": True,
                       "dtype": "f32", "data": "synthetic (random links and spinor)",
                       "config": {"workload": "D^dag D, 2048x2048 beta=8.0 kappa=0.255",
-                                 "l2": "flushed before each launch (write 256 MiB, then read "
-                                       "256 MiB)"},
+                                 "l2": f32["timing"]},
                       "roofline": {"bound": "hbm", "achieved": f32["achieved"],
                                    "peak": f32["peak"], "unit": "GB/s", "frac": f32["frac"],
                                    "kernel": f32["kernel"],
-                                   "traffic": ncu_traffic(f32["kernel"]),
-                                   "traffic_unit": "DRAM bytes per launch (ncu)"},
+                                   "traffic": f32["traffic"],
+                                   "traffic_unit": f32["traffic_unit"]},
+                      "single_launch": f32["single_launch"],
                       "f64": f64, "measured_rates": rates}), flush=True)
 
 
@@ -976,15 +1420,21 @@ def main():
     ap.add_argument("--therm", type=int, default=20)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--tight-tol", type=float, default=1e-12,
-                    help="also compare Delta H of both paths at this CG tolerance (0: skip)")
+                    help="also time both paths at this CG tolerance and compare Delta H (0: skip)")
+    ap.add_argument("--tight-steps", type=int, default=2,
+                    help="trajectories per arm of the tight-tolerance comparison")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ddagd", action="store_true")
     ap.add_argument("--cg-variant", type=int, default=-1)
     ap.add_argument("--graph", action="store_true",
                     help="replay one captured trajectory (CUDA graph) per step")
-    ap.add_argument("--workload", default="default", choices=["default", "batched", "large", "stencil", "paper"])
+    ap.add_argument("--workload", default="default",
+                    choices=["default", "batched", "large", "stencil", "paper", "sweep"])
+    ap.add_argument("--out", default=None, help="also write the JSON result to this file")
     ap.add_argument("--therm-paper", type=int, default=150,
                     help="thermalisation trajectories of the paper workload")
+    ap.add_argument("--no-h90", action="store_true",
+                    help="paper workload: skip the search for the 90 %% acceptance step size")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])
     ap.add_argument("--M", type=int, default=WORKLOAD["M"])
     ap.add_argument("--delta", type=float, default=None,
@@ -994,11 +1444,22 @@ def main():
     ap.add_argument("--sf-start", default="solve", choices=["solve", "noise"],
                     help="S_F in H at the start of a trajectory: a CG solve (default) or "
                          "eta^dag eta, exact for phi = D^dag eta (one solve fewer)")
+    ap.add_argument("--rank-selftest", action="store_true",
+                    help="run only the rank logic of a multi-rank launch (gloo, no GPU)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: start the ranks and wait for them
+        sys.exit(launch_ranks(args.gpus, sys.argv[1:]).returncode)
+    if args.rank_selftest:
+        run_rank_selftest(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "stencil":
         run_stencil(args)
+    elif args.workload == "sweep":
+        if args.delta is None:
+            args.delta = WORKLOAD["cg_delta"]
+        run_sweep(args)
     elif args.workload == "paper":
         if args.delta is None:
             args.delta = PAPER["cg_delta"]

@@ -53,3 +53,30 @@ def test_single_rank_needs_no_collective():
     import bench
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.aggregate(1, 200, 4, 2000.0) == pytest.approx(400.0)
+
+
+def test_bench_launcher_starts_two_ranks_with_the_rank_logic():
+    """`bench.py --gpus 2` starts its own ranks (torch.distributed.run on
+    127.0.0.1); the self-test runs only the rank logic on gloo: the world
+    size against --gpus, distinct local ranks, the chain shards and seeds,
+    and the max-over-ranks time behind the whole-job rate."""
+    import json
+
+    import bench
+    r = bench.launch_ranks(2, ["--gpus", "2", "--rank-selftest", "--chains", "200"],
+                           capture=True, timeout=240)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout  # rank 0 alone prints
+    out = json.loads(lines[0])
+    assert out["world"] == 2 and sorted(out["local_ranks"]) == [0, 1]
+    assert [s["first_chain"] for s in out["shards"]] == [0, 200]
+    assert len({s["seed"] for s in out["shards"]}) == 2
+    assert out["ms_max"] == 110.0  # the slower rank's time
+    assert out["value"] == pytest.approx(2 * 200 / 0.110)
+
+
+def test_bench_refuses_a_world_size_other_than_gpus():
+    import bench
+    with pytest.raises(SystemExit, match="WORLD_SIZE is 1"):
+        bench.check_world(4, 1)
