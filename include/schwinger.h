@@ -185,6 +185,33 @@ int sm_lattice_destroy(sm_lattice* lat);
  * kernel on this lattice gave up since the last check (for example a TMA copy
  * that did not complete; the affected tile was not computed). */
 int sm_lattice_check(const sm_lattice* lat, int* code);
+/* Bounds checks of the debug build (the library compiled with -DSM_DEBUG):
+ * reads and clears the count of out-of-range indices met since the last
+ * read, with the first such index and the code of the place it came from
+ * (1: a site index of a field access, checked against the site count of the
+ * call's lattice; 10-14: a neighbour of the chain-resident CG's shared-memory
+ * layout; 20-29: a halo index of the tiled D^dag D).  In the debug build an
+ * out-of-range access is redirected to index 0 instead of being made, so a
+ * kernel with an indexing error runs to its end and the error is reported
+ * here.  Synchronises the device.  In the normal build the checks are not
+ * compiled in: *violations = 0 and *first_where = -2.  No counterpart in the
+ * paper: a substitute for a memory checker, for tests.  Host pointers;
+ * SM_ERR_ARG if one is NULL. */
+int sm_debug_read(long long* violations, long long* first_index, int* first_where);
+
+/* Bound of a thread block's first wait for its TMA box copies (the interior
+ * tiles of the fused D^dag D on single-chain lattices of at least 2^18 sites
+ * too narrow for the streaming form, in sm_apply_DdagD and the grid-wide CG):
+ * `polls` polls of the copies' mbarrier, 0 <= polls <= 4194304 (the
+ * default); -1 restores the default.  A block whose first wait runs out
+ * records SM_ERR_TIMEOUT in the lattice's error word (sm_lattice_check),
+ * waits again, with the full bound, for its copies to land, and leaves its
+ * tile uncomputed instead of waiting on.  No counterpart in the paper: a
+ * control of the library's failure detection, so that a test can make the
+ * wait run out (polls = 0: every such wait gives up at once) and check that
+ * the error is reported and the context stays usable.  SM_ERR_ARG on a
+ * NULL lattice or a value out of range. */
+int sm_set_wait_limit(sm_lattice* lat, int polls);
 /* Total number of sites N of the batch. */
 long long sm_lattice_sites(const sm_lattice* lat);
 int sm_lattice_chains(const sm_lattice* lat);

@@ -91,6 +91,8 @@ _SIGS = {
     "sm_lattice_sites": (ctypes.c_longlong, [_P]),
     "sm_lattice_check": (ctypes.c_int, [_P, _P]),
     "sm_lattice_chains": (ctypes.c_int, [_P]),
+    "sm_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sm_debug_read": (ctypes.c_int, [_P, _P, _P]),
     "sm_workspace_bytes": (ctypes.c_size_t, [_P]),
     "sm_links": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "sm_apply_D": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P]),
@@ -131,7 +133,9 @@ _SIGS = {
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: the bounds-checked debug build when
+    the environment has SM_LIBRARY=debug, else the normal one."""
+    return _build.LIB_DEBUG if os.environ.get("SM_LIBRARY") == "debug" else _build.LIB
 
 
 def load() -> ctypes.CDLL:
@@ -246,6 +250,11 @@ class Lattice:
         code = ctypes.c_int()
         _check(_LIB.sm_lattice_check(self._h, ctypes.byref(code)))
         return code.value
+
+    def set_wait_limit(self, polls: int = -1):
+        """Bound of the first wait for a tile's TMA box copies
+        (sm_set_wait_limit; -1: the default)."""
+        _check(_LIB.sm_set_wait_limit(self._h, int(polls)))
 
     # ---------------------------------------------------------- helpers --
     def field(self, dtype=torch.float64):
@@ -482,6 +491,15 @@ def measure_peaks(l2_bytes: int = 48 << 20, l2_passes: int = 20) -> dict:
     _check(lib.sm_peak_smem_read(ctypes.byref(smem)))
     return {"fp64_tflops": f64.value, "fp32_tflops": f32.value, "l2_read_gbs": l2.value,
             "l2_bytes": l2_bytes, "smem_read_gbs": smem.value}
+
+
+def debug_read() -> dict:
+    """Out-of-range indices met by the debug build since the last read
+    (sm_debug_read): count, first index and the code of its place; where = -2
+    in the normal build."""
+    n, first, where = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int()
+    _check(load().sm_debug_read(ctypes.byref(n), ctypes.byref(first), ctypes.byref(where)))
+    return {"violations": n.value, "first_index": first.value, "where": where.value}
 
 
 def launch_count() -> int:

@@ -96,11 +96,15 @@ __device__ __forceinline__ Nb neighbours(int l, int L, int T, int lshift) {
   }
   const int row = t * L;
   Nb n;
-  n.l = l;
-  n.xp = row + (x + 1 == L ? 0 : x + 1);
-  n.xm = row + (x == 0 ? L - 1 : x - 1);
-  n.tp = (t + 1 == T ? 0 : t + 1) * L + x;
-  n.tm = (t == 0 ? T - 1 : t - 1) * L + x;
+  // every index is a site of the chain's shared-memory fields (checked in the
+  // debug build)
+  const int V = L * T;
+  n.l = (int)SM_IDX(l, V, 10);
+  n.xp = (int)SM_IDX(row + (x + 1 == L ? 0 : x + 1), V, 11);
+  n.xm = (int)SM_IDX(row + (x == 0 ? L - 1 : x - 1), V, 12);
+  n.tp = (int)SM_IDX((t + 1 == T ? 0 : t + 1) * L + x, V, 13);
+  n.tm = (int)SM_IDX((t == 0 ? T - 1 : t - 1) * L + x, V, 14);
+  (void)V;
   return n;
 }
 

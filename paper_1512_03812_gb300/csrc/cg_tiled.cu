@@ -40,6 +40,7 @@ struct TiledArgs {
   unsigned* counters;
   int* n_active;  // [0] chains still iterating, [1] chains due a reliable update
   int* err;
+  int spin;  // polls of the first TMA wait
   const unsigned char* grid_mask;  // hybrid solves: 0 for chains solved chain-resident
   double tol2, delta2;
   int maxit;
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(kBT) k_cgt_ap(TiledArgs a,
   const ChainInfo ci = a.g.chains[c];
   float nrm = 0.f;
   ddagd_big_tile(sm4, ci, tile, a.U, a.p, a.Ap, &nrm, tma ? &tin : nullptr, tma ? &tU : nullptr,
-                 &bar, a.err);
+                 &bar, a.err, a.spin);
   // |D p|^2: block sum, then the chain's tiles in tile order (last block)
   const double part = sum512((double)nrm);
   if (threadIdx.x == 0) {
@@ -377,6 +378,7 @@ int tiled_cg_iterate(Ctx& c, const float* U32, float* r, float* x, float* p, flo
   a.counters = c.w.counters;
   a.n_active = c.w.n_active;
   a.err = c.L->d_err;
+  a.spin = c.L->tma_spin;
   a.tol2 = tol2;
   a.delta2 = delta2;
   a.maxit = maxit;

@@ -10,7 +10,73 @@
 
 namespace sm {
 
+// Default bound, in polls of the mbarrier, of a thread block's first wait for
+// its TMA box copies (lowered per lattice by sm_set_wait_limit).
+constexpr int kTmaSpin = 1 << 22;
+
 constexpr int kBlock = 256;  // threads per site block, one site per thread
+
+// ------------------------------------------------- bounds-checked build ----
+//
+// Compiled with -DSM_DEBUG (the debug library), every site index of a field
+// access (the accessors below) is checked against the site count of the
+// call's lattice, and the neighbour and halo indices of the small-lattice
+// kernels against their shared-memory extents.  An index out of range is
+// counted, the first one recorded with a code for the place it came from,
+// and the access goes to index 0 instead: nothing traps, and the host reads
+// the record through sm_debug_read.  Each translation unit has its own copy
+// of the record (no relocatable device code); the units register their
+// set/read functions at load time.  Without SM_DEBUG the checks compile to
+// nothing.
+#ifdef SM_DEBUG
+namespace dbg {
+struct Hooks {
+  void (*set)(long long sites, cudaStream_t s);  // the extent of site-indexed fields
+  void (*take)(unsigned long long* count, long long* first, int* where);  // read and clear
+};
+int add(const Hooks& h);                            // core.cu
+void set_sites(long long sites, cudaStream_t s);    // every unit's extent, on stream s
+}  // namespace dbg
+static __device__ long long g_dbg_sites = 0x7fffffffffffffffLL;
+static __device__ unsigned long long g_dbg_count = 0;
+static __device__ long long g_dbg_first = -1;
+static __device__ int g_dbg_where = -1;
+__device__ __forceinline__ long long dbg_idx(long long i, long long n, int where) {
+  if (i >= 0 && i < n) return i;
+  if (atomicAdd(&g_dbg_count, 1ull) == 0ull) {
+    g_dbg_first = i;
+    g_dbg_where = where;
+  }
+  return 0;
+}
+static __global__ void k_dbg_set(long long n) { g_dbg_sites = n; }
+static void dbg_set(long long n, cudaStream_t s) { k_dbg_set<<<1, 1, 0, s>>>(n); }
+static void dbg_take(unsigned long long* count, long long* first, int* where) {
+  unsigned long long c = 0;
+  long long f = -1;
+  int w = -1;
+  cudaMemcpyFromSymbol(&c, g_dbg_count, sizeof c);
+  cudaMemcpyFromSymbol(&f, g_dbg_first, sizeof f);
+  cudaMemcpyFromSymbol(&w, g_dbg_where, sizeof w);
+  if (c && *count == 0) {
+    *first = f;
+    *where = w;
+  }
+  *count += c;
+  const unsigned long long zero = 0;
+  const long long none = -1;
+  const int nowhere = -1;
+  cudaMemcpyToSymbol(g_dbg_count, &zero, sizeof zero);
+  cudaMemcpyToSymbol(g_dbg_first, &none, sizeof none);
+  cudaMemcpyToSymbol(g_dbg_where, &nowhere, sizeof nowhere);
+}
+static const int g_dbg_registered = dbg::add(dbg::Hooks{&dbg_set, &dbg_take});
+#define SM_IDX(i, n, where) ::sm::dbg_idx((i), (n), (where))
+#define SM_SITE(i) ::sm::dbg_idx((i), ::sm::g_dbg_sites, 1)
+#else
+#define SM_IDX(i, n, where) (i)
+#define SM_SITE(i) (i)
+#endif
 
 // ------------------------------------------------------------ geometry ----
 
@@ -158,30 +224,30 @@ __device__ __forceinline__ R redot(Sp<R> u, Sp<R> v) {
 // Spinor fields: [N][2 spins][re, im].  FP32: one 16-byte load per site;
 // FP64: two 16-byte loads.
 __device__ __forceinline__ Sp<float> ld_sp(const float* p, long long n) {
-  const float4 v = __ldg(reinterpret_cast<const float4*>(p) + n);
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p) + SM_SITE(n));
   return {{v.x, v.y}, {v.z, v.w}};
 }
 __device__ __forceinline__ Sp<double> ld_sp(const double* p, long long n) {
-  const double2* q = reinterpret_cast<const double2*>(p) + 2 * n;
+  const double2* q = reinterpret_cast<const double2*>(p) + 2 * SM_SITE(n);
   const double2 a = __ldg(q), b = __ldg(q + 1);
   return {{a.x, a.y}, {b.x, b.y}};
 }
 // loads that bypass L1 (for fields written earlier in the same kernel by
 // other blocks never happens; used for read-write fields of the CG)
 __device__ __forceinline__ Sp<float> ld_sp_cg(const float* p, long long n) {
-  const float4 v = __ldcg(reinterpret_cast<const float4*>(p) + n);
+  const float4 v = __ldcg(reinterpret_cast<const float4*>(p) + SM_SITE(n));
   return {{v.x, v.y}, {v.z, v.w}};
 }
 __device__ __forceinline__ Sp<double> ld_sp_cg(const double* p, long long n) {
-  const double2* q = reinterpret_cast<const double2*>(p) + 2 * n;
+  const double2* q = reinterpret_cast<const double2*>(p) + 2 * SM_SITE(n);
   const double2 a = __ldcg(q), b = __ldcg(q + 1);
   return {{a.x, a.y}, {b.x, b.y}};
 }
 __device__ __forceinline__ void st_sp(float* p, long long n, Sp<float> v) {
-  reinterpret_cast<float4*>(p)[n] = make_float4(v.a.re, v.a.im, v.b.re, v.b.im);
+  reinterpret_cast<float4*>(p)[SM_SITE(n)] = make_float4(v.a.re, v.a.im, v.b.re, v.b.im);
 }
 __device__ __forceinline__ void st_sp(double* p, long long n, Sp<double> v) {
-  double2* q = reinterpret_cast<double2*>(p) + 2 * n;
+  double2* q = reinterpret_cast<double2*>(p) + 2 * SM_SITE(n);
   q[0] = make_double2(v.a.re, v.a.im);
   q[1] = make_double2(v.b.re, v.b.im);
 }
@@ -192,24 +258,24 @@ struct Lk {
   Cx<R> x, t;
 };
 __device__ __forceinline__ Lk<float> ld_lk(const float* U, long long n) {
-  const float4 v = __ldg(reinterpret_cast<const float4*>(U) + n);
+  const float4 v = __ldg(reinterpret_cast<const float4*>(U) + SM_SITE(n));
   return {{v.x, v.y}, {v.z, v.w}};
 }
 __device__ __forceinline__ Lk<double> ld_lk(const double* U, long long n) {
-  const double2* q = reinterpret_cast<const double2*>(U) + 2 * n;
+  const double2* q = reinterpret_cast<const double2*>(U) + 2 * SM_SITE(n);
   const double2 a = __ldg(q), b = __ldg(q + 1);
   return {{a.x, a.y}, {b.x, b.y}};
 }
 
 // Real link fields (q, p, F, C, v): [N][2].
 __device__ __forceinline__ double2 ld_l2(const double* a, long long n) {
-  return __ldg(reinterpret_cast<const double2*>(a) + n);
+  return __ldg(reinterpret_cast<const double2*>(a) + SM_SITE(n));
 }
 __device__ __forceinline__ double2 ld_l2_cg(const double* a, long long n) {
-  return __ldcg(reinterpret_cast<const double2*>(a) + n);
+  return __ldcg(reinterpret_cast<const double2*>(a) + SM_SITE(n));
 }
 __device__ __forceinline__ void st_l2(double* a, long long n, double2 v) {
-  reinterpret_cast<double2*>(a)[n] = v;
+  reinterpret_cast<double2*>(a)[SM_SITE(n)] = v;
 }
 
 // ------------------------------------------------- Wilson-Dirac hopping ----

@@ -101,10 +101,29 @@ int Ws::carve(const sm_lattice* L, void* ws, size_t nbytes) {
   return SM_OK;
 }
 
+#ifdef SM_DEBUG
+namespace dbg {
+static std::vector<Hooks>& hooks() {
+  static std::vector<Hooks> h;  // constructed on first use (units register at load time)
+  return h;
+}
+int add(const Hooks& h) {
+  hooks().push_back(h);
+  return (int)hooks().size();
+}
+void set_sites(long long sites, cudaStream_t s) {
+  for (const Hooks& h : hooks()) h.set(sites, s);
+}
+}  // namespace dbg
+#endif
+
 int Ctx::init(const sm_lattice* lat, void* ws, size_t nbytes, void* stream, sm_stats* stats,
                bool ws_required) {
   if (!lat) return fail(SM_ERR_ARG, "lattice is NULL");
   if (ws_required && !ws) return fail(SM_ERR_ARG, "workspace is NULL");
+#ifdef SM_DEBUG
+  dbg::set_sites(lat->N, static_cast<cudaStream_t>(stream));
+#endif
   L = lat;
   g.chains = lat->d_chains;
   g.blk_chain = lat->d_blk_chain;
@@ -587,6 +606,7 @@ int sm_lattice_create(int nchains, const int* L, const int* T, const double* bet
   lat->nblocks = blk;
   big_tile_ranges(lat);
   lat->cg_variant = -1;
+  lat->tma_spin = kTmaSpin;
   cudaGetDevice(&lat->device);
   if (const int rc = stream_ranges(lat)) {
     delete lat;
@@ -687,6 +707,34 @@ int sm_lattice_check(const sm_lattice* lat, int* code) {
   if (e != cudaSuccess) return fail(SM_ERR_CUDA, "sm_lattice_check: %s", cudaGetErrorString(e));
   *code = h;
   if (h) return fail(SM_ERR_TIMEOUT, "a bounded device-side wait gave up (code %d)", h);
+  return SM_OK;
+}
+int sm_debug_read(long long* violations, long long* first_index, int* first_where) {
+  if (!violations || !first_index || !first_where)
+    return fail(SM_ERR_ARG, "sm_debug_read: NULL argument");
+  *violations = 0;
+  *first_index = -1;
+  *first_where = -1;
+#ifdef SM_DEBUG
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(SM_ERR_CUDA, "sm_debug_read: %s", cudaGetErrorString(e));
+  unsigned long long n = 0;
+  for (const dbg::Hooks& h : dbg::hooks()) h.take(&n, first_index, first_where);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(SM_ERR_CUDA, "sm_debug_read: %s", cudaGetErrorString(e));
+  *violations = (long long)n;
+  return SM_OK;
+#else
+  *first_where = -2;  // the checks are not compiled into this library
+  return SM_OK;
+#endif
+}
+
+int sm_set_wait_limit(sm_lattice* lat, int polls) {
+  if (!lat) return fail(SM_ERR_ARG, "sm_set_wait_limit: lattice is NULL");
+  if (polls < -1 || polls > kTmaSpin)
+    return fail(SM_ERR_ARG, "sm_set_wait_limit: polls must be -1 or in [0, %d]", kTmaSpin);
+  lat->tma_spin = polls < 0 ? kTmaSpin : polls;
   return SM_OK;
 }
 int sm_lattice_chains(const sm_lattice* lat) { return lat ? lat->nchains : 0; }

@@ -90,10 +90,13 @@ __global__ void __launch_bounds__(kTX* kTY) k_ddagd_tile(const ChainInfo* __rest
   for (int i = tid; i < kDX * kDY; i += kTX * kTY) {
     const int dy = i / kDX, dx = i - dy * kDX;
     const int px = dx + 1, py = dy + 1;
-    const Sp<R> u = unpack(su[py][px]);
-    const Sp<R> o = hop_sum<false, R>(unpack(sp[py][px + 1]), unpack(sp[py][px - 1]),
-                                      unpack(sp[py + 1][px]), unpack(sp[py - 1][px]), u.a,
-                                      unpack(su[py][px - 1]).a, u.b, unpack(su[py - 1][px]).b);
+    // the halo of the staged region (checked in the debug build)
+    const int pxp = (int)SM_IDX(px + 1, kPX, 20), pxm = (int)SM_IDX(px - 1, kPX, 21);
+    const int pyp = (int)SM_IDX(py + 1, kPY, 22), pym = (int)SM_IDX(py - 1, kPY, 23);
+    const Sp<R> u = unpack(su[(int)SM_IDX(py, kUY, 24)][(int)SM_IDX(px, kUX, 25)]);
+    const Sp<R> o = hop_sum<false, R>(unpack(sp[py][pxp]), unpack(sp[py][pxm]),
+                                      unpack(sp[pyp][px]), unpack(sp[pym][px]), u.a,
+                                      unpack(su[py][pxm]).a, u.b, unpack(su[pym][px]).b);
     st[dy][dx] = pack(diag * unpack(sp[py][px]) - (R)0.5 * o);
   }
   __syncthreads();
@@ -103,10 +106,11 @@ __global__ void __launch_bounds__(kTX* kTY) k_ddagd_tile(const ChainInfo* __rest
   const int x = x0 + tx, t = t0 + ty;
   if (x >= L || t >= T) return;
   const int dx = tx + 1, dy = ty + 1;  // in st
-  const int ux = tx + 2, uy = ty + 2;  // in su
+  const int ux = (int)SM_IDX(tx + 2, kUX, 26), uy = (int)SM_IDX(ty + 2, kUY, 27);  // in su
+  const int dxp = (int)SM_IDX(dx + 1, kDX, 28), dyp = (int)SM_IDX(dy + 1, kDY, 29);
   const Sp<R> u = unpack(su[uy][ux]);
-  const Sp<R> o = hop_sum<true, R>(unpack(st[dy][dx + 1]), unpack(st[dy][dx - 1]),
-                                   unpack(st[dy + 1][dx]), unpack(st[dy - 1][dx]), u.a,
+  const Sp<R> o = hop_sum<true, R>(unpack(st[dy][dxp]), unpack(st[dy][dx - 1]),
+                                   unpack(st[dyp][dx]), unpack(st[dy - 1][dx]), u.a,
                                    unpack(su[uy][ux - 1]).a, u.b, unpack(su[uy - 1][ux]).b);
   st_sp(out, off + x + (long long)L * t, diag * unpack(st[dy][dx]) - (R)0.5 * o);
 }
@@ -118,12 +122,12 @@ __global__ void __launch_bounds__(kBT) k_ddagd_tile_big(const ChainInfo* __restr
                                                         float* __restrict__ out,
                                                         const __grid_constant__ CUtensorMap tin,
                                                         const __grid_constant__ CUtensorMap tU,
-                                                        int tma, int* err) {
+                                                        int tma, int* err, int spin) {
   extern __shared__ __align__(128) float4 sm4[];
   __shared__ __align__(8) unsigned long long bar;
   const int4 tile = tiles[blockIdx.x];
   ddagd_big_tile(sm4, chains[tile.x], tile, U, in, out, nullptr, tma ? &tin : nullptr,
-                 tma ? &tU : nullptr, &bar, err);
+                 tma ? &tU : nullptr, &bar, err, spin);
 }
 
 // Streaming form: one strip per warp (stream.cuh).
@@ -313,7 +317,7 @@ int launch_ddagd(Ctx& c, const R* U, const R* in, R* out) {
     const bool tma = make_tile_tmaps(c.L, (const float*)in, (const float*)U, &tin, &tU);
     k_ddagd_tile_big<<<c.L->ntiles_big, kBT, smem, c.s>>>(
         c.L->d_chains, c.L->d_tiles_big, (const float*)U, (const float*)in, (float*)out, tin, tU,
-        tma ? 1 : 0, c.L->d_err);
+        tma ? 1 : 0, c.L->d_err, c.L->tma_spin);
     return launched(c.st, "ddagd_tile_big");
   }
   k_ddagd_tile<R><<<c.L->ntiles, kTX * kTY, 0, c.s>>>(c.L->d_chains, c.L->d_tiles, U, in, out);

@@ -45,6 +45,7 @@ struct sm_lattice {
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;
   int* d_err;  // device-side error word (a bounded wait that gave up)
+  int tma_spin;  // polls of the first wait for a tile's TMA box copies (sm_set_wait_limit)
   int device;
   int* h_pinned;  // small pinned host buffer for per-call readbacks
   cudaEvent_t ev[2];  // readback events of the CG loop

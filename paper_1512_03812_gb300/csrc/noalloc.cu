@@ -149,6 +149,9 @@ extern "C" int sm_apply_DdagD_noalloc(int L, int T, double m0, const void* U, co
   const int rc = scratch_address(&scratch);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+#ifdef SM_DEBUG
+  dbg::set_sites(V, s);
+#endif
   if (prec == SM_F64)
     return ddagd_single<double>(L, T, m0, (const double*)U, (const double*)in, (double*)out,
                                 (double*)scratch, s);

@@ -32,7 +32,6 @@ constexpr size_t kBigSmemBytes = sizeof(float4) * (kBPX * kBPY + kBUX * kBUY + k
 // origins use x = 2 (x0 - 2), always even: 16-byte aligned.
 constexpr unsigned kTmaInBytes = 2 * kBPX * kBPY * 8;
 constexpr unsigned kTmaUBytes = 2 * kBUX * kBUY * 8;
-constexpr int kTmaSpin = 1 << 22;  // bounded wait for the box copies
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -40,10 +39,12 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
 
 // Stages `in` and U of an interior tile by two box copies completing on
 // `bar`; returns false (and records err) if they did not complete within
-// kTmaSpin polls of the barrier.
+// `spin` polls of the barrier (kTmaSpin unless the lattice's limit was
+// lowered).  The wait after a give-up, for copies still landing in this
+// block's shared memory, keeps its full bound whatever `spin` is.
 __device__ __forceinline__ bool tma_stage(float4* sp, float4* su, const CUtensorMap* tin,
                                           const CUtensorMap* tU, int x0, int t0,
-                                          unsigned long long* bar, int* err) {
+                                          unsigned long long* bar, int* err, int spin) {
   const unsigned b = smem_u32(bar);
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(b) : "memory");
@@ -78,7 +79,7 @@ __device__ __forceinline__ bool tma_stage(float4* sp, float4* su, const CUtensor
     return ok;
   };
   unsigned done = 0;
-  for (int i = 0; i < kTmaSpin && !done; ++i) done = poll();
+  for (int i = 0; i < spin && !done; ++i) done = poll();
   if (!done) {
     if (threadIdx.x == 0 && err) atomicOr(err, 1);
     // the copies may still be landing in this block's shared memory: wait for
@@ -103,7 +104,7 @@ __device__ __forceinline__ void ddagd_big_tile(float4* sm4, const ChainInfo& ci,
                                                const CUtensorMap* tin = nullptr,
                                                const CUtensorMap* tU = nullptr,
                                                unsigned long long* bar = nullptr,
-                                               int* err = nullptr) {
+                                               int* err = nullptr, int spin = kTmaSpin) {
 
   float4* sp = sm4;                   // [kBPY][kBPX]
   float4* su = sp + kBPX * kBPY;      // [kBUY][kBUX]
@@ -115,7 +116,7 @@ __device__ __forceinline__ void ddagd_big_tile(float4* sm4, const ChainInfo& ci,
   const float4* U4 = reinterpret_cast<const float4*>(U) + off;
   const bool interior = x0 >= 2 && x0 + kBX + 2 <= L && t0 >= 2 && t0 + kBY + 2 <= T;
   if (interior && tin) {
-    if (!tma_stage(sp, su, tin, tU, x0, t0, bar, err)) return;
+    if (!tma_stage(sp, su, tin, tU, x0, t0, bar, err, spin)) return;
   } else if (interior) {
     const float4* pin = in4 + (x0 - 2) + (long long)L * (t0 - 2);
     const float4* pU = U4 + (x0 - 2) + (long long)L * (t0 - 2);

@@ -197,3 +197,38 @@ def test_hybrid_batch_fused_iteration(torch):
         for c in range(len(shapes)):
             assert np.linalg.norm(b.chain(r, c)) <= 1.0000001e-10 * np.linalg.norm(b.chain(rhs, c))
     assert b.lat.check() == 0
+
+
+def test_tma_wait_give_up_is_reported_and_recovers(torch):
+    """The bounded wait of a block for its TMA box copies, made to run out on
+    purpose (limit 0: every interior tile of the 130 x 2048 lattice gives up
+    at once; the copies themselves still land and the second, fully bounded
+    wait lets them before the block leaves).  The lattice reports
+    SM_ERR_TIMEOUT, the context stays usable, and with the default limit
+    restored the same call matches the oracle."""
+    import paper_1512_03812_gb300 as P
+    from paper_1512_03812_gb300 import binding as B
+    L, T = 130, 2048
+    m0 = sw.kappa_to_m0(0.24)
+    lat = P.Lattice(L, T, 2.0, m0)
+    with pytest.raises(B.SchwingerError):
+        lat.set_wait_limit(-2)
+    with pytest.raises(B.SchwingerError):
+        lat.set_wait_limit(1 << 23)
+    q = I.hot_links(L, T, 93)
+    psi = I.spinor(L, T, 94)
+    U64, U32 = lat.links(torch.tensor(q, device="cuda"))
+    p32 = torch.tensor(psi, device="cuda").to(torch.complex64)
+    assert lat.check() == 0
+    lat.set_wait_limit(0)
+    lat.apply_DdagD(U32, p32)
+    with pytest.raises(B.SchwingerError) as e:
+        lat.check()
+    assert e.value.code == B.SM_ERR_TIMEOUT
+    assert lat.check() == 0  # the word was cleared by the read
+    lat.set_wait_limit(-1)
+    out = lat.apply_DdagD(U32, p32).cpu().numpy().reshape(T, L, 2)
+    assert lat.check() == 0
+    olat = sw.Lattice(L, T, 2.0, m0)
+    ref = sw.apply_DdagD(olat, sw.links(q.reshape(T, L, 2)), psi.reshape(T, L, 2))
+    assert rel_err(out, ref) < 4e-6

@@ -47,7 +47,8 @@ def test_noalloc_matches_workspace_entry_point_twice(torch, L, T):
 def test_noalloc_rejects_lattices_beyond_its_scratch(torch):
     from paper_1512_03812_gb300 import binding
     L = T = 1024  # 1048576 sites > 262144 (FP64) and > 524288 (FP32)
-    U = torch.zeros((8, 2), dtype=torch.complex128, device="cuda")
-    psi = torch.zeros((8, 2), dtype=torch.complex128, device="cuda")
-    with pytest.raises(binding.SchwingerError, match="exceed"):
-        binding.apply_DdagD_noalloc(L, T, 0.0, U, psi)
+    for dt in (torch.complex128, torch.complex64):
+        U = torch.zeros((L * T, 2), dtype=dt, device="cuda")
+        psi = torch.zeros((L * T, 2), dtype=dt, device="cuda")
+        with pytest.raises(binding.SchwingerError, match="exceed"):
+            binding.apply_DdagD_noalloc(L, T, 0.0, U, psi)
