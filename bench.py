@@ -830,9 +830,13 @@ def run_other(args):
 SWEEP = {
     "workload": "64x64 beta=2.0 kappa=0.26, 200 momentum sets from one thermalised "
                 "configuration per point, tau=1, outer n in {4,6,8,10}, inner m in {1,2,4} "
-                "(nested schemes), mixed CG (FP32 + FP64 reliable updates) against FP64 CG, "
+                "(nested schemes), plus n in {16,24} for the order in h, mixed CG (FP32 + FP64 "
+                "reliable updates) against FP64 CG, "
                 "tol 1e-10 (1e-12 for the S_F of H)",
     "chains": 200, "n": (4, 6, 8, 10), "M": (1, 2, 4),
+    # larger n for the order of Delta H in h (at n <= 10 most schemes are at or
+    # beyond their stability limit on this configuration)
+    "n_order": (16, 24),
     "schemes": [("leapfrog", None), ("five_stage", "2mn"), ("five_stage_fg", None),
                 ("nested_leapfrog", None), ("nested_fg", None), ("adapted_nested_fg", None)],
 }
@@ -879,7 +883,7 @@ def run_sweep(args):
         Ms = SWEEP["M"] if "nested" in scheme else (1,)
         lam = P.LAMBDA_2MN if variant == "2mn" else 1.0 / 6.0
         for M in Ms:
-            for n in SWEEP["n"]:
+            for n in SWEEP["n"] + SWEEP["n_order"]:
                 p = torch.randn((N, 2), generator=g, device=dev, dtype=torch.float64)
                 e = torch.view_as_complex(torch.randn((N, 2, 2), generator=g, device=dev,
                                                       dtype=torch.float64) * math.sqrt(0.5))
@@ -916,16 +920,26 @@ def run_sweep(args):
                 rows.append(row)
                 log(f"sweep {row['scheme']} n={n} M={M}: acc {row['mixed']['acceptance']:.3f}/"
                     f"{row['fp64']['acceptance']:.3f} dev {row['max_abs_dH_mixed_minus_fp64']:.2e}")
+    # the order of Delta H in h from the points inside the stability region
+    # (median |Delta H| below 1: beyond it |Delta H| grows exponentially
+    # and no power law holds)
     slopes = []
     keys = sorted({(r["scheme"], r["M"]) for r in rows}, key=str)
     for sch, M in keys:
         rs = [r for r in rows if r["scheme"] == sch and r["M"] == M]
-        hs = [r["h"] for r in rs]
-        slopes.append({"scheme": sch, "M": M,
-                       "slope_mixed": _slope(hs, [r["mixed"]["median_abs_dH"] for r in rs]),
-                       "slope_fp64": _slope(hs, [r["fp64"]["median_abs_dH"] for r in rs])})
+        st = {}
+        for name in ("mixed", "fp64"):
+            ok = [r for r in rs if r[name]["median_abs_dH"] is not None
+                  and r[name]["median_abs_dH"] < 1.0]
+            st[name] = (_slope([r["h"] for r in ok], [r[name]["median_abs_dH"] for r in ok]),
+                        [r["n"] for r in ok])
+        slopes.append({"scheme": sch, "M": M, "slope_mixed": st["mixed"][0],
+                       "slope_fp64": st["fp64"][0], "fitted_n": st["fp64"][1]})
     devs = [r["max_abs_dH_mixed_minus_fp64"] for r in rows
             if r["max_abs_dH_mixed_minus_fp64"] is not None]
+    devs_stable = [r["max_abs_dH_mixed_minus_fp64"] for r in rows
+                   if r["max_abs_dH_mixed_minus_fp64"] is not None
+                   and (r["fp64"]["median_abs_dH"] or 1e9) < 1.0]
     res = {"metric": "mixed against FP64 over step sizes", "workload": SWEEP["workload"],
            "data": "synthetic (own thermalised start, seeded momenta/noise)",
            "chains": B, "cg_tol": W["cg_tol"], "cg_tol_action": W["cg_tol_action"],
@@ -935,6 +949,7 @@ def run_sweep(args):
                       "fp64_over_mixed": round(t_d / t_m, 2) if t_m else None,
                       "total": round(time.time() - t0, 1)},
            "max_abs_dH_mixed_minus_fp64_overall": max(devs) if devs else None,
+           "max_abs_dH_mixed_minus_fp64_stable_points": max(devs_stable) if devs_stable else None,
            "same_decisions_overall": float(np.mean([r["same_decisions"] for r in rows])),
            "slope_of_median_abs_dH_in_h": slopes, "points": rows}
     line = json.dumps(res)

@@ -619,10 +619,20 @@ __device__ __forceinline__ unsigned krank() {
 // slower: the FP32 iterate in global memory, updated by vector reductions at
 // L2 to free its registers (27 % slower), and the thread's own p kept in
 // registers besides shared memory (spills; 24 % slower).
+// Blocks per SM the register budget is sized for: two where a block's part
+// of the chain takes at most half an SM's shared memory (clusters of parts
+// of 96 KB), else one.
+template <int L, int T, int K>
+constexpr int pair_min_blocks() {
+  return (K > 1 && 48 * L * T / K <= 116 * 1024) ? 2 : 1;
+}
+
 template <int R, int NT, int L, int T, int K>
-__global__ void __launch_bounds__(NT, K == 2 ? 2 : 1) k_cg_chain_pair(ChainCgArgs a) {
+__global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_pair(ChainCgArgs a) {
   static_assert(L % 2 == 0 && T % K == 0 && L * T == 2 * R * NT * K,
                 "one thread per two columns of R rows");
+  static_assert(NT % 32 == 0 && (T / K) % R == 0 && NT == (L / 2) * (T / K / R),
+                "whole warps; the threads tile the part's rows in strips of R");
   constexpr int H = T / K, V = H * L, HL = L / 2;  // rows and sites of a block's part
   extern __shared__ float4 smem[];
   __shared__ float red[2][NT / 32];
@@ -1288,8 +1298,17 @@ int chain_cg_prepare(const sm_lattice* L, const sm_cg_params& cg) {
     e = cudaFuncSetAttribute(k_cg_chain_pair<8, 128, 64, 64, 2>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem / 2);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_cg_chain_pair<8, 256, 128, 128, 4>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 4096 * 16);
+    e = cudaFuncSetAttribute(k_cg_chain_pair<4, 256, 128, 128, 8>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 2048 * 16);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_chain_pair<2, 64, 16, 16, 1>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 256 * 16);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_chain_pair<4, 128, 32, 32, 1>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 1024 * 16);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_chain_pair<4, 288, 48, 48, 1>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 2304 * 16);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_cg_chain_mixed<1, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
@@ -1344,14 +1363,75 @@ int chain_cg_accumulate(Ctx& c) {
   return launched(c.st, "cg_accumulate");
 }
 
-// The chains of a mixed batch that fit the shared-memory form, solved by the
-// strided kernel (one block each) on c.s; the other chains are untouched.
+int chain_group_kind(const ChainInfo& ci) {
+  if (ci.L != ci.T) return 0;
+  switch (ci.L) {
+    case 16: return 1;
+    case 32: return 2;
+    case 48: return 3;
+    case 64: return 4;
+    default: return 0;
+  }
+}
+
+// Launches the mixed chain-resident solve of one kernel group on stream s,
+// the group's chains longest first (by their previous solve).  Column pairs
+// per shape (threads x rows per thread): 16 x 16: 64 x 2, 32 x 32: 128 x 4,
+// 48 x 48: 288 x 4, 64 x 64: 256 x 8 (each 2 columns wide; at 64 x 64 the
+// 256 x 8 form solves faster than 512 x 4 also when its chain has the SM to
+// itself).  Other shapes: the strided kernel.  The kernel depends only on
+// the chain's shape, so a chain's result does not depend on the rest of its
+// batch.
+static int launch_group(Ctx& c, const ChainCgArgs& a0, int g, cudaStream_t s) {
+  const sm_lattice* L = c.L;
+  ChainCgArgs a = a0;
+  const int n = L->group_count[g], kind = L->group_kind[g];
+  a.list = L->d_group_list + L->group_begin[g];
+  if (kind != 0 && n > 1 && n <= kOrderMax) {
+    // the groups order their chains into the end of the order buffer, after
+    // the entries of the chains outside the groups (the 128 x 128 clusters,
+    // ordered at the same time on another stream, write the start of it)
+    int grouped = 0;
+    for (int h = 0; h < L->ngroups; ++h) grouped += L->group_count[h];
+    int* ord = c.w.order + (L->nchains - grouped) + L->group_begin[g];
+    k_chain_order<<<1, 1024, 0, s>>>(c.w.cgc, a.list, ord, n);
+    const int rc = launched(c.st, "chain_order");
+    if (rc) return rc;
+    a.list = ord;
+  }
+  const size_t smem = (size_t)3 * L->group_vmax[g] * sizeof(float4);
+  cudaError_t e = cudaSuccess;
+  auto go = [&](auto kern, int nt) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) kern<<<dim3((unsigned)n), dim3(nt), smem, s>>>(a);
+  };
+  switch (kind) {
+    case 1: go(k_cg_chain_pair<2, 64, 16, 16, 1>, 64); break;
+    case 2: go(k_cg_chain_pair<4, 128, 32, 32, 1>, 128); break;
+    case 3: go(k_cg_chain_pair<4, 288, 48, 48, 1>, 288); break;
+    case 4: go(k_cg_chain_pair<8, 256, 64, 64, 1>, 256); break;
+    default: {
+      const int vmax = L->group_vmax[g];
+      if (vmax <= 1024)
+        go(k_cg_chain_mixed<1, 1024>, 1024);
+      else if (vmax <= 2048)
+        go(k_cg_chain_mixed<2, 1024>, 1024);
+      else
+        go(k_cg_chain_mixed<8, 512>, 512);
+    }
+  }
+  if (e != cudaSuccess) return fail(SM_ERR_CUDA, "chain CG attribute: %s", cudaGetErrorString(e));
+  return launched(c.st, "cg_chain_group");
+}
+
+// The chains of at most 4096 sites of a mixed batch (the others untouched):
+// one launch per kernel group, the first on c.s, the others on the groups'
+// own streams, forked from and joined back into c.s.
 int chain_cg_launch_list(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
                          const sm_cg_params& cg, double* dx) {
   const sm_lattice* L = c.L;
   ChainCgArgs a{};
   a.chains = L->d_chains;
-  a.list = L->d_small_list;
   a.U32 = U32;
   a.U64 = U64;
   a.b = b;
@@ -1363,24 +1443,22 @@ int chain_cg_launch_list(Ctx& c, const double* U64, const float* U32, const doub
   a.tol2 = cg.tol * cg.tol;
   a.delta2 = cg.delta * cg.delta;
   a.maxit = cg.maxit;
-  int vmax = 0;
-  for (const ChainInfo& ci : L->chains)
-    if (ci.L * ci.T <= kChainMaxVolume && ci.L * ci.T > vmax) vmax = ci.L * ci.T;
-  const size_t smem = (size_t)3 * vmax * sizeof(float4);
-  const dim3 grid((unsigned)L->nsmall);
-  cudaError_t e = cudaSuccess;
-  auto go = [&](auto kern, int nt) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) kern<<<grid, dim3(nt), smem, c.s>>>(a);
-  };
-  if (vmax <= 1024)
-    go(k_cg_chain_mixed<1, 1024>, 1024);
-  else if (vmax <= 2048)
-    go(k_cg_chain_mixed<2, 1024>, 1024);
-  else
-    go(k_cg_chain_mixed<8, 512>, 512);
-  if (e != cudaSuccess) return fail(SM_ERR_CUDA, "chain CG attribute: %s", cudaGetErrorString(e));
-  return launched(c.st, "cg_chain_mixed_list");
+  if (L->ngroups > 1) {
+    cudaError_t e = cudaEventRecord(L->gev_fork, c.s);
+    for (int g = 1; g < L->ngroups && e == cudaSuccess; ++g)
+      e = cudaStreamWaitEvent(L->gstream[g], L->gev_fork, 0);
+    if (e != cudaSuccess) return fail(SM_ERR_CUDA, "chain CG groups fork: %s", cudaGetErrorString(e));
+  }
+  for (int g = 0; g < L->ngroups; ++g) {
+    const int rc = launch_group(c, a, g, g == 0 ? c.s : L->gstream[g]);
+    if (rc) return rc;
+  }
+  for (int g = 1; g < L->ngroups; ++g) {
+    cudaError_t e = cudaEventRecord(L->gev_join[g], L->gstream[g]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c.s, L->gev_join[g], 0);
+    if (e != cudaSuccess) return fail(SM_ERR_CUDA, "chain CG groups join: %s", cudaGetErrorString(e));
+  }
+  return SM_OK;
 }
 
 int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
@@ -1425,8 +1503,8 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
       ab.list = c.w.order;
     }
     if (sq128)
-      e = launch_cluster<4>(k_cg_chain_pair<8, 256, 128, 128, 4>, L->nbig, 256,
-                            (size_t)3 * 4096 * 16, c.s, ab);
+      e = launch_cluster<8>(k_cg_chain_pair<4, 256, 128, 128, 8>, L->nbig, 256,
+                            (size_t)3 * 2048 * 16, c.s, ab);
     else
       e = launch_cluster<4>(k_cg_chain_cluster<8, 512, 4>, L->nbig, 512, (size_t)3 * 4096 * 16,
                             c.s, ab);
@@ -1447,6 +1525,12 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
       if (e == cudaSuccess) kern<<<grid, dim3(nt), smem, c.s>>>(a);
     };
     int v = L->cg_variant;
+    if (v < 0 && L->ngroups > 0) {
+      // not pinned: one launch per kernel group
+      const int rc = chain_cg_launch_list(c, U64, U32, b, x, cg, dx);
+      if (rc) return rc;
+      return SM_OK;
+    }
     if (v < 0 || !chain_variant_applies(L, v)) v = 0;
     if (v == 3) {
       e = launch_cluster<2>(k_cg_chain_cluster<8, 256, 2>, L->nchains, 256, smem / 2, c.s, a);

@@ -4,6 +4,7 @@
 // link-field linear combinations and the per-chain energy sums.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -660,6 +661,38 @@ int sm_lattice_create(int nchains, const int* L, const int* T, const double* bet
     e = cudaMemcpy(lat->d_grid_mask, lat->grid_mask.data(), nchains, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !small.empty())
     e = cudaMemcpy(lat->d_small_list, small.data(), sizeof(int) * small.size(), cudaMemcpyHostToDevice);
+  // the chains of at most 4096 sites by kernel group, each group's chains
+  // in batch order
+  {
+    std::vector<int> glist;
+    lat->ngroups = 0;
+    for (int kind = 0; kind < sm_lattice::kGroups; ++kind) {
+      const int begin = (int)glist.size();
+      int vmax = 0;
+      for (int c : small)
+        if (chain_group_kind(lat->chains[c]) == kind) {
+          glist.push_back(c);
+          vmax = std::max(vmax, lat->chains[c].L * lat->chains[c].T);
+        }
+      if ((int)glist.size() > begin) {
+        const int g = lat->ngroups++;
+        lat->group_kind[g] = kind;
+        lat->group_begin[g] = begin;
+        lat->group_count[g] = (int)glist.size() - begin;
+        lat->group_vmax[g] = vmax;
+      }
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&lat->d_group_list, sizeof(int) * (glist.empty() ? 1 : glist.size()));
+    if (e == cudaSuccess && !glist.empty())
+      e = cudaMemcpy(lat->d_group_list, glist.data(), sizeof(int) * glist.size(),
+                     cudaMemcpyHostToDevice);
+    for (int g = 1; g < lat->ngroups && e == cudaSuccess; ++g) {
+      e = cudaStreamCreateWithFlags(&lat->gstream[g], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lat->gev_join[g], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lat->gev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&lat->nsm, cudaDevAttrMultiProcessorCount, lat->device);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&lat->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(lat->d_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&lat->side, cudaStreamNonBlocking);
@@ -684,6 +717,12 @@ int sm_lattice_destroy(sm_lattice* lat) {
   if (lat->d_small_list) cudaFree(lat->d_small_list);
   if (lat->d_big_list) cudaFree(lat->d_big_list);
   if (lat->side) cudaStreamDestroy(lat->side);
+  if (lat->d_group_list) cudaFree(lat->d_group_list);
+  for (int g = 0; g < sm_lattice::kGroups; ++g) {
+    if (lat->gstream[g]) cudaStreamDestroy(lat->gstream[g]);
+    if (lat->gev_join[g]) cudaEventDestroy(lat->gev_join[g]);
+  }
+  if (lat->gev_fork) cudaEventDestroy(lat->gev_fork);
   if (lat->ev_fork) cudaEventDestroy(lat->ev_fork);
   if (lat->ev_join) cudaEventDestroy(lat->ev_join);
   if (lat->d_tiles_big) cudaFree(lat->d_tiles_big);

@@ -40,6 +40,18 @@ struct sm_lattice {
   int* d_small_list;
   int nbig;           // chains of the 4-block cluster shape (128 x 128), and their list
   int* d_big_list;
+  // the chains of at most 4096 sites grouped by the kernel that serves their
+  // shape (chain_group_kind): group g is d_group_list[group_begin[g] ..
+  // group_begin[g] + group_count[g]); a mixed chain-resident solve of these
+  // chains is one launch per group, the first group on the caller's stream,
+  // the others on streams of their own
+  static constexpr int kGroups = 5;
+  int ngroups;
+  int group_kind[kGroups], group_begin[kGroups], group_count[kGroups], group_vmax[kGroups];
+  int* d_group_list;
+  cudaStream_t gstream[kGroups];
+  cudaEvent_t gev_fork, gev_join[kGroups];
+  int nsm;            // multiprocessors of the device
   unsigned char* d_grid_mask;
   std::vector<unsigned char> grid_mask;
   cudaStream_t side;
@@ -188,6 +200,10 @@ int chain_cg_prepare(const sm_lattice* L, const sm_cg_params& cg);
 // True if every solve with these parameters takes the chain-resident path.
 bool chain_cg_selected(const sm_lattice* L, const sm_cg_params& cg);
 int chain_cg_accumulate(Ctx& c);
+// The kernel group of a chain of at most 4096 sites: 1-4 the column-pair
+// kernels of 16 x 16, 32 x 32, 48 x 48 and 64 x 64 chains, 0 the strided
+// kernel (any other shape).
+int chain_group_kind(const sm::ChainInfo& ci);
 int chain_cg_launch_list(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
                          const sm_cg_params& cg, double* dx = nullptr);
 

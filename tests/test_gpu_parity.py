@@ -240,8 +240,9 @@ def test_hmc_sf_start_from_noise(torch, prec):
 
 def test_mixed_batch_with_128x128_chains(torch):
     """A batch of small chains and 128 x 128 chains is solved chain-resident
-    throughout: the small ones one block each, the large ones by 4-block
-    clusters (rows exchanged through distributed shared memory)."""
+    throughout: the small ones one block each (one launch per shape group),
+    the large ones by 8-block clusters (rows exchanged through distributed
+    shared memory)."""
     import paper_1512_03812_gb300 as P
     dims = [(128, 128), (64, 64), (16, 16), (128, 128), (48, 48)]
     b = batch(torch, dims=dims, betas=(2.0, 1.0, 4.0, 2.0, 1.5), kappas=(0.24, 0.22, 0.2, 0.25, 0.23))
@@ -264,6 +265,47 @@ def test_mixed_batch_with_128x128_chains(torch):
                            "adapted_nested_fg", 0.2, 1, M=2, solver=sw.Solver(1e-13))
     assert abs(dH[0] - ro.dH) < 1e-6, (dH[0], ro.dH)
     assert b.lat.check() == 0
+
+
+def test_chain_groups_every_small_shape(torch):
+    """A batch of small chains of several shapes is solved as one launch per
+    kernel group, each on its own stream: column pairs for 16 x 16 (64
+    threads x 2 rows), 32 x 32 (128 x 4), 48 x 48 (288 x 4) and 64 x 64 (256
+    x 8), the strided kernel for the rest (here 24 x 20).  Every chain meets
+    the FP64 true residual, agrees with the FP64 solve, and its result is
+    bitwise the one it gets solved alone (the kernel depends only on the
+    chain's shape); one short trajectory of the batch matches the oracle."""
+    import paper_1512_03812_gb300 as P
+    dims = [(32, 32), (16, 16), (48, 48), (64, 64), (24, 20), (16, 16), (48, 48), (32, 32)]
+    betas = (2.0, 1.0, 4.0, 2.0, 1.5, 3.0, 1.0, 2.0)
+    kappas = (0.24, 0.26, 0.22, 0.25, 0.23, 0.21, 0.25, 0.26)
+    b = batch(torch, dims=dims, betas=betas, kappas=kappas, seed=13)
+    q, phi = b.q(), b.spinor()
+    U64, U32 = b.lat.links(b.dev(q))
+    x64, _, _ = b.lat.cg_solve(U64, U32, b.dev(phi), cg(1e-12))
+    mcg = P.CG(tol=1e-10, prec="mixed", delta=0.01, algo="chain")
+    xm, iters, relres = b.lat.cg_solve(U64, U32, b.dev(phi), mcg)
+    assert (relres <= 1e-10).all(), relres
+    r = b.dev(phi) - b.lat.apply_DdagD(U64, xm)
+    for c in range(len(dims)):
+        assert np.linalg.norm(b.chain(r, c)) <= 1.0000001e-10 * np.linalg.norm(b.chain(phi, c))
+        assert rel_err(b.chain(xm, c), b.chain(x64, c)) < 1e-8
+        L, T = dims[c]
+        solo = P.Lattice(L, T, betas[c], b.m0[c])
+        sl = slice(b.off[c], b.off[c + 1])
+        U64s, U32s = solo.links(b.dev(q[sl]))
+        xs, its, _ = solo.cg_solve(U64s, U32s, b.dev(phi[sl]), mcg)
+        assert its[0] == iters[c]
+        assert torch.equal(xs, xm[sl])
+    p, eta = b.p(), b.eta()
+    md = P.MD(scheme="adapted_nested_fg", tau=0.2, n=1, M=2,
+              cg=P.CG(tol=1e-12, prec="mixed", delta=0.01))
+    dH, H0, acc = b.lat.hmc_trajectory(b.dev(q), b.dev(p), b.dev(eta), 0.5, md)
+    for c in (0, 1, 2, 4):
+        ro = ig.hmc_trajectory(b.olat[c], b.chain(q, c), b.chain(p, c), b.chain(eta, c), 0.5,
+                               "adapted_nested_fg", 0.2, 1, M=2, solver=sw.Solver(1e-13))
+        assert abs(dH[c] - ro.dH) < 1e-6, (c, dH[c], ro.dH)
+        assert bool(acc[c]) == ro.accepted
 
 
 def test_large_chains_of_other_shapes(torch):
