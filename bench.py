@@ -658,6 +658,52 @@ OTHER_WORKLOADS = {
 }
 
 
+BATCHED_KERNELS = {16: "k_cg_chain_pair<2,64,16,16,1>", 32: "k_cg_chain_pair<4,128,32,32,1>",
+                   48: "k_cg_chain_pair<4,288,48,48,1>", 64: "k_cg_chain_pair<8,256,64,64,1>",
+                   128: "k_cg_chain_pair<4,256,128,128,8> (8-block clusters)"}
+
+
+def batched_kernels(torch, P, lat, q, Ls, betas, m0, cgp, smem_peak):
+    """The shape groups' kernels one at a time: each group's chains as a
+    lattice of their own with the batch's current links, one solve of a
+    seeded right-hand side timed with CUDA events after a warm-up solve, and
+    the group's shared-memory bytes (152 per site-iteration) over that time.
+    The longest chain of a group sets its launch's duration, so the mean and
+    largest iteration counts are given beside it."""
+    g = torch.Generator(device=lat.device)
+    g.manual_seed(77)
+    out = []
+    off = lat.offsets
+    U64, U32 = lat.links(q)
+    b = torch.view_as_complex(torch.randn((lat.N, 2, 2), generator=g, device=lat.device,
+                                          dtype=torch.float64)).contiguous()
+    for side in sorted(set(Ls)):
+        idx = [c for c in range(len(Ls)) if Ls[c] == side]
+        rows = torch.tensor(np.concatenate([np.arange(off[c], off[c + 1]) for c in idx]),
+                            device=lat.device)
+        sub = P.Lattice([side] * len(idx), [side] * len(idx), np.asarray(betas)[idx],
+                        np.asarray(m0)[idx], device=lat.device)
+        u64, u32, bs = U64[rows].contiguous(), U32[rows].contiguous(), b[rows].contiguous()
+        sub.cg_solve(u64, u32, bs, cgp)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, its, _ = sub.cg_solve(u64, u32, bs, cgp)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        si = int(np.sum(its)) * side * side
+        gbs = SMEM_BYTES_PAIR * si / (ms / 1e3) / 1e9
+        out.append({"side": side, "kernel": BATCHED_KERNELS.get(side, "k_cg_chain_mixed"),
+                    "chains": len(idx), "ms_per_solve": round(ms, 3), "site_iters": si,
+                    "iters_mean": round(float(np.mean(its)), 1), "iters_max": int(np.max(its)),
+                    "bytes_per_site_iter": SMEM_BYTES_PAIR, "achieved": round(gbs, 1),
+                    "frac": round(gbs / smem_peak, 4)})
+        del sub
+    return out
+
+
 def run_other(args):
     """Trajectory throughput of the batched-chain or the large-lattice
     configuration (one JSON line; thermalisation untimed, as for the
@@ -783,21 +829,23 @@ def run_other(args):
     if args.workload == "batched":
         # every chain is chain-resident: the iteration data stays in shared
         # memory, so the bound is shared-memory bandwidth (HBM-equivalent
-        # bytes beside it for context)
-        # small chains take the strided kernel (320 B), the 128 x 128 ones the
-        # 4-block column-pair cluster (152 B): the lower figure is used for
-        # all, so `achieved` is a lower bound
+        # bytes beside it for context).  Every shape of this batch has a
+        # column-pair kernel (152 B per site-iteration): 16, 32, 48 and 64
+        # one block per chain, 128 x 128 8-block clusters
         sach = SMEM_BYTES_PAIR * prof["site_iters"] / ksec / 1e9 if ksec else 0.0
         roofline = dict({"bound": "smem",
-                         "kernel": "chain-resident CG (one block per small chain, 4-block "
-                                   "column-pair clusters for 128x128 chains)",
+                         "kernel": "chain-resident CG (one launch per shape group: column pairs "
+                                   "16x16, 32x32, 48x48, 64x64 one block per chain; 128x128 "
+                                   "8-block clusters)",
                          "achieved": round(sach, 1), "peak": round(rates["smem_read_gbs"], 1),
                          "unit": "GB/s", "frac": round(sach / rates["smem_read_gbs"], 4),
                          "peak_source": "measured in this run (sm_peak_smem_read)",
                          "bytes_per_site_iter": SMEM_BYTES_PAIR,
                          "hbm_equivalent": {"achieved": round(ach, 1), "peak": hbm,
                                             "frac": round(ach / hbm, 4),
-                                            "bytes_per_site_iter": bps, "peak_source": src}},
+                                            "bytes_per_site_iter": bps, "peak_source": src},
+                         "per_kernel": batched_kernels(torch, P, lat, q, Ls, betas, m0, cgp,
+                                                       rates["smem_read_gbs"])},
                         **common)
     else:
         # the 2048^2 lattice takes the fused streaming iteration: F reads r,

@@ -160,8 +160,13 @@ class Solver:
         self.tol = tol
         self.maxit = maxit
         self.inversions = 0
+        self.inversions_by_m0 = {}  # the same count split by the operator's bare mass
         self.cg_calls = 0
         self.cg_iterations = 0
+
+    def _count(self, lat, k):
+        self.inversions += k
+        self.inversions_by_m0[lat.m0] = self.inversions_by_m0.get(lat.m0, 0) + k
 
     def cg(self, lat: Lattice, U: np.ndarray, b: np.ndarray) -> np.ndarray:
         self.cg_calls += 1
@@ -187,17 +192,17 @@ class Solver:
 
     def DdagD_inv(self, lat, U, b):
         """(D^dag D)^{-1} b: counted as D^dag^{-1} then D^{-1}."""
-        self.inversions += 2
+        self._count(lat, 2)
         return self.cg(lat, U, b)
 
     def Dinv(self, lat, U, y):
         """D^{-1} y = (D^dag D)^{-1} D^dag y."""
-        self.inversions += 1
+        self._count(lat, 1)
         return self.cg(lat, U, apply_D(lat, U, y, dagger=True))
 
     def Ddaginv(self, lat, U, y):
         """D^dag^{-1} y = D (D^dag D)^{-1} y."""
-        self.inversions += 1
+        self._count(lat, 1)
         return apply_D(lat, U, self.cg(lat, U, y))
 
 
@@ -428,6 +433,73 @@ def shifted_force(lat: Lattice, q: np.ndarray, phi: np.ndarray, solver: Solver,
     return force(lat, links(q - (h * h / 24.0) * F0), phi, solver, part)
 
 
+# ------------------------------------- determinant split over two masses ---
+#
+# The paper's outlook (Conclusions) partitions the action into more than two
+# parts by factorising the fermion determinant, so that the most expensive
+# part needs the force-gradient information and the cheaper, faster parts
+# only leapfrog steps.  The factorisation used is the mass split of
+# Hasenbusch (Phys. Lett. B 519 (2001) 177): with D_h the Wilson-Dirac
+# operator at the heavier bare mass m0 + dm,
+#   det(D^dag D) = det(D_h^dag D_h) * det(W^dag W),  W = D D_h^{-1},
+# each factor represented by a pseudofermion:
+#   S_h = phi_h^dag (D_h^dag D_h)^{-1} phi_h      (heavy part)
+#   S_r = phi_r^dag (W^dag W)^{-1} phi_r = psi^dag (D^dag D)^{-1} psi,
+#         psi = D_h^dag phi_r                        (ratio part, the light one).
+
+def heavy_lattice(lat: Lattice, dm: float) -> Lattice:
+    """The same lattice and couplings with the bare mass m0 + dm (D_h)."""
+    return Lattice(lat.L, lat.T, lat.beta, lat.m0 + dm, lat.bc)
+
+
+def ratio_vectors(lat: Lattice, lat_h: Lattice, U: np.ndarray, phi_r: np.ndarray,
+                  solver: Solver):
+    """psi = D_h^dag phi_r, X = (D^dag D)^{-1} psi and a = D X - phi_r."""
+    psi = apply_D(lat_h, U, phi_r, dagger=True)
+    X = solver.DdagD_inv(lat, U, psi)
+    a = apply_D(lat, U, X) - phi_r
+    return psi, X, a
+
+
+def ratio_action(lat: Lattice, lat_h: Lattice, U: np.ndarray, phi_r: np.ndarray,
+                 solver: Solver) -> float:
+    """S_r = phi_r^dag D_h (D^dag D)^{-1} D_h^dag phi_r."""
+    psi = apply_D(lat_h, U, phi_r, dagger=True)
+    X = solver.DdagD_inv(lat, U, psi)
+    return float(np.vdot(psi, X).real)
+
+
+def ratio_force(lat: Lattice, lat_h: Lattice, U: np.ndarray, phi_r: np.ndarray,
+                solver: Solver) -> np.ndarray:
+    """dS_r/dq.  The hopping terms of D and D_h are the same, so with
+    dD = dD/dq_mu(n):  dS_r = 2 Re[phi_r^dag dD X] - 2 Re[(D X)^dag dD X]
+    = -2 Re[a^dag dD X]: the bilinear of Eq. force_fermion with chi -> a,
+    xi -> X."""
+    _, X, a = ratio_vectors(lat, lat_h, U, phi_r, solver)
+    return fermion_force_from(lat, U, a, X)
+
+
+def ratio_force_and_gradient(lat: Lattice, lat_h: Lattice, U: np.ndarray, phi_r: np.ndarray,
+                             solver: Solver):
+    """F_r and C_r = grad |F_r|^2 = 2 (Hess S_r) F_r.  Along a direction v,
+    dX = -(D^dag D)^{-1}(s_1 + D^dag s_2) and da = dD X + D dX with
+    s_1 = (dD_v)^dag a, s_2 = (dD_v) X: the vectors Z_1, Z_2 of Eq. Z12 with
+    (chi, xi) -> (a, X), so C_r is Eq. CFF with the same substitution."""
+    _, X, a = ratio_vectors(lat, lat_h, U, phi_r, solver)
+    F = fermion_force_from(lat, U, a, X)
+    return F, c_fermion(lat, U, a, X, F, solver)
+
+
+def heatbath_split(lat: Lattice, lat_h: Lattice, U: np.ndarray, eta_r: np.ndarray,
+                   eta_h: np.ndarray, solver: Solver):
+    """The two pseudofermions from Gaussian noise: phi_h = D_h^dag eta_h and
+    phi_r = W^dag eta_r = D_h^dag^{-1} D^dag eta_r, so that S_h = eta_h^dag
+    eta_h and S_r = eta_r^dag eta_r at the start."""
+    phi_h = apply_D(lat_h, U, eta_h, dagger=True)
+    phi_r = solver.Ddaginv(lat_h, U, apply_D(lat, U, eta_r, dagger=True))
+    return phi_r, phi_h
+
+
 def kinetic(p: np.ndarray) -> float:
     """1/2 sum p^2 (Eq. schwinger)."""
     return float(0.5 * np.sum(p * p))
@@ -437,3 +509,12 @@ def hamiltonian(lat: Lattice, q: np.ndarray, p: np.ndarray, phi: np.ndarray, sol
     """H = 1/2 sum p^2 + S_G + S_F (Eq. schwinger)."""
     U = links(q)
     return kinetic(p) + gauge_action(lat, U) + fermion_action(lat, U, phi, solver)
+
+
+def hamiltonian_split(lat: Lattice, lat_h: Lattice, q: np.ndarray, p: np.ndarray,
+                      phi_r: np.ndarray, phi_h: np.ndarray, solver: Solver) -> float:
+    """H = 1/2 sum p^2 + S_G + S_h + S_r with the determinant split over two
+    masses."""
+    U = links(q)
+    return (kinetic(p) + gauge_action(lat, U) + fermion_action(lat_h, U, phi_h, solver)
+            + ratio_action(lat, lat_h, U, phi_r, solver))
