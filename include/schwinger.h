@@ -72,6 +72,14 @@ extern "C" {
 #define SM_PART_GAUGE 1
 #define SM_PART_FERMION 2
 #define SM_PART_FULL 3
+/* With the fermion determinant split over two masses (sm_lattice_set_heavy;
+ * the factorisation the paper's Conclusions call for, in the form of
+ * Hasenbusch's mass split): det(D^dag D) = det(D_h^dag D_h) det(W^dag W),
+ * W = D D_h^{-1}, D_h the Wilson-Dirac operator at the bare mass m0 + dm,
+ *   S_h = phi_h^dag (D_h^dag D_h)^{-1} phi_h                (heavy part)
+ *   S_r = phi_r^dag D_h (D^dag D)^{-1} D_h^dag phi_r        (ratio part). */
+#define SM_PART_HEAVY 4
+#define SM_PART_RATIO 8
 
 /* integration schemes of Sec. 2 */
 #define SM_LEAPFROG 0            /* Eq. leap */
@@ -83,6 +91,14 @@ extern "C" {
 #define SM_ADAPTED_NESTED_FG 6   /* Eq. ad_5stage_multi_fg (C_FF outside, leapfrog inside) */
 #define SM_ELEVEN_STAGE 7        /* Eq. 11_stage, with the weights of Eq. (71) of Omelyan,
                                     Mryglod and Folk (2003) that the paper cites */
+/* Three time scales on the determinant split over two masses (the paper's
+ * Conclusions: more than two parts, force-gradient information only for the
+ * most expensive one, leapfrog for the fast ones).  B3 = S_r outside, B2 =
+ * S_h in the middle (md.M2 leapfrog steps per middle block), B1 = S_G inside
+ * (md.M leapfrog steps per gauge block). */
+#define SM_NESTED3_LEAPFROG 8    /* Eq. leap_multi on three levels */
+#define SM_ADAPTED_NESTED3_FG 9  /* Eq. ad_5stage_multi_fg with S_r outside and C of S_r
+                                    alone, leapfrog levels of S_h and S_G inside */
 
 /* how a force-gradient kick obtains C */
 #define SM_FG_EXACT 0    /* exact C via one extra CG (Eq. CFF, Eq. Z12) */
@@ -136,6 +152,8 @@ typedef struct {
   int sf_start;       /* S_F in H at the start of sm_hmc_trajectory: SM_SF_SOLVE (a CG
                          solve, like the end) or SM_SF_NOISE (eta^dag eta, exact for
                          phi = D^dag eta; one solve fewer) */
+  int M2;             /* three-level schemes: leapfrog steps of the heavy part per middle
+                         block (>= 1; ignored by the other schemes) */
 } sm_md_params;
 
 /* Counters accumulated over one call (zeroed by the call). */
@@ -180,6 +198,24 @@ int sm_profile_read(double* iter_ms, double* res_ms, long long* batched_iters,
 int sm_lattice_create(int nchains, const int* L, const int* T, const double* beta,
                       const double* m0, sm_lattice** out);
 int sm_lattice_destroy(sm_lattice* lat);
+/* Splits the fermion determinant of every chain over the masses m0_c and
+ * m0_c + dm (SM_PART_HEAVY, SM_PART_RATIO, the three-level schemes): keeps a
+ * second copy of the lattice's tables at the heavy masses (allocates; call
+ * it at set-up, and size workspaces with sm_workspace_bytes afterwards: the
+ * split needs two more spinor fields).  dm > 0; calling it again changes dm.
+ * Then:
+ *   sm_force / sm_fermion_force-like calls with part SM_PART_HEAVY take phi =
+ *     phi_h, with SM_PART_RATIO phi = phi_r (one part per call);
+ *   sm_force_gradient with SM_PART_RATIO returns C of S_r alone;
+ *   sm_md_trajectory / sm_md_step with a three-level scheme take phi =
+ *     [phi_r; phi_h] (2N spinors, phi_r first);
+ *   sm_hmc_trajectory / sm_hmc_graph_create with a three-level scheme take
+ *     eta = [eta_r; eta_h] (2N spinors): phi_h = D_h^dag eta_h and
+ *     phi_r = D_h^dag^{-1} D^dag eta_r, so that S_h = eta_h^dag eta_h and
+ *     S_r = eta_r^dag eta_r at the start; H = K + S_G + S_h + S_r.
+ * SM_ERR_ARG if dm <= 0 or not finite, SM_ERR_CUDA on an allocation failure. */
+int sm_lattice_set_heavy(sm_lattice* lat, double dm);
+
 /* Reads and clears the lattice's device error word after synchronising the
  * device: nonzero (and SM_ERR_TIMEOUT) if a bounded device-side wait of a
  * kernel on this lattice gave up since the last check (for example a TMA copy

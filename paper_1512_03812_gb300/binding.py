@@ -35,10 +35,15 @@ SCHEMES = {
     "nested_fg": 5,
     "adapted_nested_fg": 6,
     "eleven_stage": 7,
+    "nested3_leapfrog": 8,
+    "adapted_nested3_fg": 9,
 }
+THREE_LEVEL = ("nested3_leapfrog", "adapted_nested3_fg")
 FG_EXACT, FG_SHIFTED = 0, 1
 CG_VARIANTS = 8  # kernel variants of the chain-resident mixed CG (SM_CG_VARIANTS)
-PARTS = {"gauge": PART_GAUGE, "fermion": PART_FERMION, "full": PART_FULL}
+PART_HEAVY, PART_RATIO = 4, 8
+PARTS = {"gauge": PART_GAUGE, "fermion": PART_FERMION, "full": PART_FULL, "heavy": PART_HEAVY,
+         "ratio": PART_RATIO}
 LAMBDA_2MN = 0.1931833275037836
 
 
@@ -61,7 +66,7 @@ class MdParams(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int), ("tau", ctypes.c_double), ("n", ctypes.c_int),
                 ("M", ctypes.c_int), ("lambda_", ctypes.c_double), ("fg", ctypes.c_int),
                 ("merge_kicks", ctypes.c_int), ("cg", CgParams), ("tol_action", ctypes.c_double),
-                ("sf_start", ctypes.c_int)]
+                ("sf_start", ctypes.c_int), ("M2", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -92,6 +97,7 @@ _SIGS = {
     "sm_lattice_check": (ctypes.c_int, [_P, _P]),
     "sm_lattice_chains": (ctypes.c_int, [_P]),
     "sm_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sm_lattice_set_heavy": (ctypes.c_int, [_P, ctypes.c_double]),
     "sm_debug_read": (ctypes.c_int, [_P, _P, _P]),
     "sm_workspace_bytes": (ctypes.c_size_t, [_P]),
     "sm_links": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -203,13 +209,14 @@ class MD:
     cg: CG = None
     tol_action: float = 0.0  # tolerance of the S_F solves of H (0: cg.tol)
     sf_start: str = "solve"  # S_F at the start of a trajectory: "solve" or "noise" (eta^dag eta)
+    M2: int = 1              # three-level schemes: heavy leapfrog steps per middle block
 
     def c(self) -> MdParams:
         cg = self.cg or CG()
         return MdParams(SCHEMES[self.scheme], self.tau, self.n, self.M, self.lam,
                         {"exact": FG_EXACT, "shifted": FG_SHIFTED}[self.fg],
                         1 if self.merge_kicks else 0, cg.c(), self.tol_action,
-                        {"solve": 0, "noise": 1}[self.sf_start])
+                        {"solve": 0, "noise": 1}[self.sf_start], self.M2)
 
 
 class Lattice:
@@ -250,6 +257,17 @@ class Lattice:
         code = ctypes.c_int()
         _check(_LIB.sm_lattice_check(self._h, ctypes.byref(code)))
         return code.value
+
+    def set_heavy(self, dm: float):
+        """Splits the fermion determinant over the masses m0 and m0 + dm
+        (sm_lattice_set_heavy) and enlarges the workspace for it.  Parts
+        "heavy" and "ratio" and the three-level schemes need it; their
+        pseudofermion and noise tensors are then (2N, 2): phi_r / eta_r in
+        the first N rows, phi_h / eta_h in the last N."""
+        _check(_LIB.sm_lattice_set_heavy(self._h, float(dm)))
+        self.heavy_dm = float(dm)
+        self.ws_bytes = int(_LIB.sm_workspace_bytes(self._h))
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
 
     def set_wait_limit(self, polls: int = -1):
         """Bound of the first wait for a tile's TMA box copies

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -64,6 +65,7 @@ size_t Ws::bytes(const sm_lattice* L) {
   b += align256(3 * nc * sizeof(int));
   b += align256(2 * sizeof(int));
   b += align256(nc * sizeof(int));
+  if (L->heavy) b += 2 * align256(N * 32);  // phi_h, psi
   return b;
 }
 
@@ -98,6 +100,11 @@ int Ws::carve(const sm_lattice* L, void* ws, size_t nbytes) {
   acc = reinterpret_cast<int*>(take(3 * nc * sizeof(int)));
   n_active = reinterpret_cast<int*>(take(2 * sizeof(int)));
   order = reinterpret_cast<int*>(take(nc * sizeof(int)));
+  phi_h = psi = nullptr;
+  if (L->heavy) {
+    phi_h = reinterpret_cast<double*>(take(N * 32));
+    psi = reinterpret_cast<double*>(take(N * 32));
+  }
   h_n_active = L->h_pinned;
   return SM_OK;
 }
@@ -439,6 +446,14 @@ __global__ void __launch_bounds__(kBlock) k_lincomb(Geo g, double* y, const doub
   st_l2(y, s.n, r);
 }
 
+// Spinors: y = w + a x.
+__global__ void __launch_bounds__(kBlock) k_spinor_lincomb(Geo g, double* y, const double* w,
+                                                           double a, const double* x) {
+  SITE_PROLOGUE
+  if (!s.valid) return;
+  st_sp(y, s.n, ld_sp_cg(w, s.n) + a * ld_sp_cg(x, s.n));
+}
+
 // dst = src on the chains whose mask is nonzero.
 __global__ void __launch_bounds__(kBlock) k_copy_masked(Geo g, double* dst, const double* src,
                                                         const int* mask) {
@@ -540,6 +555,10 @@ int launch_lincomb(Ctx& c, double* y, const double* w, double a, const double* x
                    const double* z) {
   k_lincomb<<<c.grid(), kBlock, 0, c.s>>>(c.g, y, w, a, x, b, z);
   return launched(c.st, "lincomb");
+}
+int launch_spinor_lincomb(Ctx& c, double* y, const double* w, double a, const double* x) {
+  k_spinor_lincomb<<<c.grid(), kBlock, 0, c.s>>>(c.g, y, w, a, x);
+  return launched(c.st, "spinor_lincomb");
 }
 int launch_drift(Ctx& c, double* q, const double* p, double eps) {
   k_lincomb<<<c.grid(), kBlock, 0, c.s>>>(c.g, q, q, eps, p, 0.0, nullptr);
@@ -717,6 +736,7 @@ int sm_lattice_destroy(sm_lattice* lat) {
   if (lat->d_small_list) cudaFree(lat->d_small_list);
   if (lat->d_big_list) cudaFree(lat->d_big_list);
   if (lat->side) cudaStreamDestroy(lat->side);
+  if (lat->heavy) sm_lattice_destroy(lat->heavy);
   if (lat->d_group_list) cudaFree(lat->d_group_list);
   for (int g = 0; g < sm_lattice::kGroups; ++g) {
     if (lat->gstream[g]) cudaStreamDestroy(lat->gstream[g]);
@@ -743,6 +763,12 @@ int sm_lattice_check(const sm_lattice* lat, int* code) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(&h, lat->d_err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(lat->d_err, 0, sizeof(int));
+  if (e == cudaSuccess && lat->heavy) {  // the heavy copy's kernels record there
+    int hh = 0;
+    e = cudaMemcpy(&hh, lat->heavy->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(lat->heavy->d_err, 0, sizeof(int));
+    h |= hh;
+  }
   if (e != cudaSuccess) return fail(SM_ERR_CUDA, "sm_lattice_check: %s", cudaGetErrorString(e));
   *code = h;
   if (h) return fail(SM_ERR_TIMEOUT, "a bounded device-side wait gave up (code %d)", h);
@@ -767,6 +793,34 @@ int sm_debug_read(long long* violations, long long* first_index, int* first_wher
   *first_where = -2;  // the checks are not compiled into this library
   return SM_OK;
 #endif
+}
+
+int sm_lattice_set_heavy(sm_lattice* lat, double dm) {
+  if (!lat) return fail(SM_ERR_ARG, "sm_lattice_set_heavy: lattice is NULL");
+  if (!(dm > 0.0) || !std::isfinite(dm))
+    return fail(SM_ERR_ARG, "sm_lattice_set_heavy: dm must be positive and finite");
+  const int n = lat->nchains;
+  std::vector<int> L(n), T(n);
+  std::vector<double> beta(n), m0(n);
+  for (int c = 0; c < n; ++c) {
+    L[c] = lat->chains[c].L;
+    T[c] = lat->chains[c].T;
+    beta[c] = lat->chains[c].beta;
+    m0[c] = lat->chains[c].m0 + dm;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess && dev != lat->device) e = cudaSetDevice(lat->device);
+  if (e != cudaSuccess) return fail(SM_ERR_CUDA, "sm_lattice_set_heavy: %s", cudaGetErrorString(e));
+  sm_lattice* h = nullptr;
+  const int rc = sm_lattice_create(n, L.data(), T.data(), beta.data(), m0.data(), &h);
+  if (dev != lat->device) cudaSetDevice(dev);
+  if (rc) return rc;
+  h->cg_variant = lat->cg_variant;
+  if (lat->heavy) sm_lattice_destroy(lat->heavy);
+  lat->heavy = h;
+  lat->heavy_dm = dm;
+  return SM_OK;
 }
 
 int sm_set_wait_limit(sm_lattice* lat, int polls) {

@@ -52,6 +52,10 @@ struct sm_lattice {
   cudaStream_t gstream[kGroups];
   cudaEvent_t gev_fork, gev_join[kGroups];
   int nsm;            // multiprocessors of the device
+  // the fermion determinant split over two masses (sm_lattice_set_heavy):
+  // the same chains at the bare masses m0 + heavy_dm, or NULL
+  sm_lattice* heavy;
+  double heavy_dm;
   unsigned char* d_grid_mask;
   std::vector<unsigned char> grid_mask;
   cudaStream_t side;
@@ -101,6 +105,10 @@ struct Ws {
   // real link fields [N][2]
   double *F, *C, *F2, *qs, *qsave, *pw, *v;
   double* sinp;  // [N] sine of the plaquette angle (gauge kick)
+  // the split over two masses (lattices with a heavy copy only, carved after
+  // everything else, so that the heavy copy's own carve of the same buffer
+  // leaves them alone): the heavy pseudofermion and psi = D_h^dag phi_r
+  double *phi_h, *psi;
   // reductions
   double* partials;    // [4][nblocks]
   unsigned* counters;  // [nchains]
@@ -164,6 +172,8 @@ int launch_gauge_hvp(Ctx& c, const double* q, const double* v, double* C, bool a
 int launch_axpy_links(Ctx& c, double* y, const double* x, double a, const double* z, double b);
 int launch_drift(Ctx& c, double* q, const double* p, double eps);
 // y = w + a x + b z on real link fields (w, z may be NULL).
+// Spinors: y = w + a x.
+int launch_spinor_lincomb(Ctx& c, double* y, const double* w, double a, const double* x);
 int launch_lincomb(Ctx& c, double* y, const double* w, double a, const double* x, double b,
                    const double* z);
 int launch_energies(Ctx& c, const double* q, const double* p, const double* phi, const double* xi,

@@ -36,6 +36,36 @@ static int check_part(int part) {
   return SM_OK;
 }
 
+// One part of the determinant split (a call of the single-part entry points).
+static int check_split_part(const sm_lattice* L, int part) {
+  if (part != SM_PART_HEAVY && part != SM_PART_RATIO) return check_part(part);
+  if (!L->heavy) return fail(SM_ERR_ARG, "part %d needs sm_lattice_set_heavy first", part);
+  return SM_OK;
+}
+
+static bool three_level(int scheme) {
+  return scheme == SM_NESTED3_LEAPFROG || scheme == SM_ADAPTED_NESTED3_FG;
+}
+
+// The context of the lattice's heavy copy (the same chains at m0 + dm): the
+// same stream, statistics and workspace (the heavy copy's carve of the
+// buffer gives every common field the same address), its own chain table.
+static Ctx heavy_ctx(const Ctx& c) {
+  Ctx h = c;
+  h.L = c.L->heavy;
+  h.g.chains = h.L->d_chains;
+  h.g.blk_chain = h.L->d_blk_chain;
+  h.chain_flags.clear();
+  return h;
+}
+
+// Failures of the heavy copy's solves count as the chain's own.
+static void merge_flags(Ctx& c, const Ctx& h) {
+  if (h.chain_flags.empty()) return;
+  if (c.chain_flags.empty()) c.chain_flags.assign(h.chain_flags.size(), 0);
+  for (size_t i = 0; i < h.chain_flags.size(); ++i) c.chain_flags[i] |= h.chain_flags[i];
+}
+
 // U64 (and U32 for mixed solves) from q.
 static int make_links(Ctx& c, const double* q, double* U64, float* U32, const sm_cg_params& cg) {
   return launch_links(c, q, U64, cg.prec == SM_MIXED ? U32 : nullptr);
@@ -52,15 +82,61 @@ static int chi_xi(Ctx& c, const double* U64, const float* U32, const double* phi
   return have ? SM_OK : launch_dslash<double>(c, U64, c.w.xi, c.w.chi, false, nullptr, 0.0);
 }
 
+// The heavy part: xi = (D_h^dag D_h)^{-1} phi_h and chi = D_h xi in c.w.xi,
+// c.w.chi (Eq. chi_xi_vectors at the heavy mass).
+static int chi_xi_heavy(Ctx& c, const double* U64, const float* U32, const double* phi_h,
+                        const sm_cg_params& cg) {
+  Ctx h = heavy_ctx(c);
+  bool have = false;
+  int rc = cg_solve(h, U64, U32, phi_h, c.w.xi, cg, nullptr, nullptr, c.w.chi, &have);
+  merge_flags(c, h);
+  if (rc) return rc;
+  c.st->inversions += 2;
+  c.st->force_evals++;
+  return have ? SM_OK : launch_dslash<double>(h, U64, c.w.xi, c.w.chi, false, nullptr, 0.0);
+}
+
+// The ratio part: psi = D_h^dag phi_r (c.w.psi), X = (D^dag D)^{-1} psi
+// (c.w.xi) and a = D X - phi_r (c.w.chi).  dS_r/dq is the bilinear of
+// Eq. force_fermion with chi -> a, xi -> X (the hopping terms of D and D_h
+// are the same), and the force-gradient term of S_r is Eq. CFF / Z12 with the
+// same substitution.
+static int ratio_vectors(Ctx& c, const double* U64, const float* U32, const double* phi_r,
+                         const sm_cg_params& cg) {
+  Ctx h = heavy_ctx(c);
+  SM_TRY(launch_dslash<double>(h, U64, phi_r, c.w.psi, true, nullptr, 0.0));
+  bool have = false;
+  SM_TRY(cg_solve(c, U64, U32, c.w.psi, c.w.xi, cg, nullptr, nullptr, c.w.chi, &have));
+  c.st->inversions += 2;
+  c.st->force_evals++;
+  if (have) return launch_spinor_lincomb(c, c.w.chi, c.w.chi, -1.0, phi_r);
+  return launch_dslash<double>(c, U64, c.w.xi, c.w.chi, false, phi_r, -1.0);
+}
+
 // The force of `part` at q (links U64/U32 of q): written to F (if not NULL)
-// and/or applied as the kick p -= eps F (if p is not NULL).
+// and/or applied as the kick p -= eps F (if p is not NULL).  phi is the
+// pseudofermion of the fermion part (or the ratio part), phi_h the heavy one.
 static int force_at(Ctx& c, const double* q, const double* U64, const float* U32,
                     const double* phi, int part, const sm_cg_params& cg, double* F, double* p,
-                    double eps) {
-  if (part & SM_PART_GAUGE) SM_TRY(launch_gauge_kick(c, q, p, eps, F, false));
+                    double eps, const double* phi_h = nullptr) {
+  bool acc = false;  // F holds a part already
+  if (part & SM_PART_GAUGE) {
+    SM_TRY(launch_gauge_kick(c, q, p, eps, F, false));
+    acc = true;
+  }
   if (part & SM_PART_FERMION) {
     SM_TRY(chi_xi(c, U64, U32, phi, cg));
-    SM_TRY(launch_fermion_kick(c, U64, c.w.chi, c.w.xi, p, eps, F, (part & SM_PART_GAUGE) != 0));
+    SM_TRY(launch_fermion_kick(c, U64, c.w.chi, c.w.xi, p, eps, F, acc));
+    acc = true;
+  }
+  if (part & SM_PART_HEAVY) {
+    SM_TRY(chi_xi_heavy(c, U64, U32, phi_h, cg));
+    SM_TRY(launch_fermion_kick(c, U64, c.w.chi, c.w.xi, p, eps, F, acc));
+    acc = true;
+  }
+  if (part & SM_PART_RATIO) {
+    SM_TRY(ratio_vectors(c, U64, U32, phi, cg));
+    SM_TRY(launch_fermion_kick(c, U64, c.w.chi, c.w.xi, p, eps, F, acc));
   }
   return SM_OK;
 }
@@ -91,20 +167,23 @@ static int hess_times(Ctx& c, const double* q, const double* U64, const float* U
 }
 
 // F of `part` into c.w.F and C = 2 Hess F into C (Eq. force_gradient).
+// The ratio part alone (part == SM_PART_RATIO) leaves (a, X) in c.w.chi,
+// c.w.xi, where the fermion branch of hess_times reads them.
 static int force_and_gradient(Ctx& c, const double* q, const double* U64, const float* U32,
                               const double* phi, int part, const sm_cg_params& cg, double* C) {
   SM_TRY(force_at(c, q, U64, U32, phi, part, cg, c.w.F, nullptr, 0.0));
-  return hess_times(c, q, U64, U32, part, c.w.F, cg, C);
+  return hess_times(c, q, U64, U32, part == SM_PART_RATIO ? SM_PART_FERMION : part, c.w.F, cg,
+                    C);
 }
 
 // F(q - (h^2/24) F(q)) of `part` into F and/or as the kick p -= eps F.
 static int shifted_force(Ctx& c, const double* q, const double* U64, const float* U32,
                          const double* phi, int part, double h, const sm_cg_params& cg, double* F,
-                         double* p, double eps) {
-  SM_TRY(force_at(c, q, U64, U32, phi, part, cg, c.w.F, nullptr, 0.0));
+                         double* p, double eps, const double* phi_h = nullptr) {
+  SM_TRY(force_at(c, q, U64, U32, phi, part, cg, c.w.F, nullptr, 0.0, phi_h));
   SM_TRY(launch_lincomb(c, c.w.qs, q, -h * h / 24.0, c.w.F, 0.0, nullptr));
-  if (part & SM_PART_FERMION) SM_TRY(make_links(c, c.w.qs, c.w.U64s, c.w.U32s, cg));
-  return force_at(c, c.w.qs, c.w.U64s, c.w.U32s, phi, part, cg, F, p, eps);
+  if (part & ~SM_PART_GAUGE) SM_TRY(make_links(c, c.w.qs, c.w.U64s, c.w.U32s, cg));
+  return force_at(c, c.w.qs, c.w.U64s, c.w.U32s, phi, part, cg, F, p, eps, phi_h);
 }
 
 // ------------------------------------------------------------- schedules --
@@ -132,6 +211,16 @@ static void inner_fg(std::vector<Op>& o, double h, int M) {
     o.push_back({OP_FG, SM_PART_GAUGE, hm});
     o.push_back({OP_DRIFT, 0, hm / 2.0});
     o.push_back({OP_KICK, SM_PART_GAUGE, hm / 6.0});
+  }
+}
+
+// Delta_2(h): M2 leapfrog steps of the heavy part, each with M gauge
+// leapfrog steps inside (the middle level of the three-level schemes).
+static void middle_lf(std::vector<Op>& o, double h, int M2, int M) {
+  for (int i = 0; i < M2; ++i) {
+    o.push_back({OP_KICK, SM_PART_HEAVY, h / (2.0 * M2)});
+    inner_lf(o, h / M2, M);
+    o.push_back({OP_KICK, SM_PART_HEAVY, h / (2.0 * M2)});
   }
 }
 
@@ -202,6 +291,22 @@ static int build_step(std::vector<Op>& o, const sm_md_params& md, double h) {
       }
       return SM_OK;
     }
+    case SM_NESTED3_LEAPFROG: {
+      const int R = SM_PART_RATIO;
+      o.push_back({OP_KICK, R, h / 2});
+      middle_lf(o, h, md.M2, M);
+      o.push_back({OP_KICK, R, h / 2});
+      return SM_OK;
+    }
+    case SM_ADAPTED_NESTED3_FG: {
+      const int R = SM_PART_RATIO;
+      o.push_back({OP_KICK, R, h / 6});
+      middle_lf(o, h / 2, md.M2, M);
+      o.push_back({OP_FG, R, h});
+      middle_lf(o, h / 2, md.M2, M);
+      o.push_back({OP_KICK, R, h / 6});
+      return SM_OK;
+    }
     default:
       return fail(SM_ERR_ARG, "unknown scheme %d", md.scheme);
   }
@@ -219,10 +324,15 @@ static void merge(std::vector<Op>& o) {
   o.swap(m);
 }
 
-static int check_md(const sm_md_params* md) {
+static int check_md(const sm_md_params* md, const sm_lattice* L = nullptr) {
   if (!md) return fail(SM_ERR_ARG, "md params are NULL");
-  if (md->scheme < SM_LEAPFROG || md->scheme > SM_ELEVEN_STAGE)
+  if (md->scheme < SM_LEAPFROG || md->scheme > SM_ADAPTED_NESTED3_FG)
     return fail(SM_ERR_ARG, "unknown scheme %d", md->scheme);
+  if (three_level(md->scheme)) {
+    if (md->M2 < 1) return fail(SM_ERR_ARG, "M2 = %d < 1", md->M2);
+    if (L && !L->heavy)
+      return fail(SM_ERR_ARG, "three-level schemes need sm_lattice_set_heavy first");
+  }
   if (md->M < 1) return fail(SM_ERR_ARG, "M = %d < 1", md->M);
   if (md->fg != SM_FG_EXACT && md->fg != SM_FG_SHIFTED) return fail(SM_ERR_ARG, "bad fg mode");
   if (md->sf_start != SM_SF_SOLVE && md->sf_start != SM_SF_NOISE)
@@ -233,11 +343,11 @@ static int check_md(const sm_md_params* md) {
 // Executes `ops` on (q, p).  Links are refreshed lazily, only before an
 // operation that needs the fermion force.
 static int execute(Ctx& c, const std::vector<Op>& ops, double* q, double* p, const double* phi,
-                   const sm_md_params& md) {
+                   const sm_md_params& md, const double* phi_h) {
   bool links_ok = false;
   const sm_cg_params& cg = md.cg;
   for (const Op& op : ops) {
-    if ((op.k != OP_DRIFT) && (op.part & SM_PART_FERMION) && !links_ok) {
+    if ((op.k != OP_DRIFT) && (op.part & ~SM_PART_GAUGE) && !links_ok) {
       SM_TRY(make_links(c, q, c.w.U64, c.w.U32, cg));
       links_ok = true;
     }
@@ -247,7 +357,7 @@ static int execute(Ctx& c, const std::vector<Op>& ops, double* q, double* p, con
         links_ok = false;
         break;
       case OP_KICK:
-        SM_TRY(force_at(c, q, c.w.U64, c.w.U32, phi, op.part, cg, nullptr, p, op.eps));
+        SM_TRY(force_at(c, q, c.w.U64, c.w.U32, phi, op.part, cg, nullptr, p, op.eps, phi_h));
         break;
       case OP_FG: {
         // e^{(2/3) h B + (1/72) h^3 C}:  p <- p - (2h/3) F + (h^3/72) C
@@ -257,7 +367,7 @@ static int execute(Ctx& c, const std::vector<Op>& ops, double* q, double* p, con
           SM_TRY(launch_lincomb(c, p, p, -2.0 * h / 3.0, c.w.F, h * h * h / 72.0, c.w.C));
         } else {
           SM_TRY(shifted_force(c, q, c.w.U64, c.w.U32, phi, op.part, h, cg, nullptr, p,
-                               2.0 * h / 3.0));
+                               2.0 * h / 3.0, phi_h));
         }
         break;
       }
@@ -266,12 +376,15 @@ static int execute(Ctx& c, const std::vector<Op>& ops, double* q, double* p, con
   return SM_OK;
 }
 
+// phi: the pseudofermion; for the three-level schemes phi_r, with phi_h
+// given separately (phi_h NULL: phi holds [phi_r; phi_h]).
 static int md_run(Ctx& c, double* q, double* p, const double* phi, const sm_md_params& md,
-                  double h, int nsteps) {
+                  double h, int nsteps, const double* phi_h = nullptr) {
   std::vector<Op> ops;
   for (int i = 0; i < nsteps; ++i) SM_TRY(build_step(ops, md, h));
   if (md.merge_kicks) merge(ops);
-  return execute(c, ops, q, p, phi, md);
+  if (three_level(md.scheme) && !phi_h) phi_h = phi + 4 * (size_t)c.L->N;
+  return execute(c, ops, q, p, phi, md, phi_h);
 }
 
 }  // namespace sm
@@ -314,15 +427,16 @@ int sm_force(const sm_lattice* lat, const double* q, const double* phi, int part
              void* stream) {
   Ctx c;
   SM_TRY(c.init(lat, ws, ws_bytes, stream, stats));
-  SM_TRY(check_part(part));
+  SM_TRY(check_split_part(lat, part));
   SM_TRY(fields_ok({q, F}, "sm_force"));
-  if (part & SM_PART_FERMION) {
+  if (part & ~SM_PART_GAUGE) {
     SM_TRY(check_cg(cg));
     SM_TRY(fields_ok({phi}, "sm_force"));
     SM_TRY(make_links(c, q, c.w.U64, c.w.U32, *cg));
   }
   sm_cg_params dummy{1e-10, 1, SM_F64, 0.1, SM_CG_AUTO};
-  SM_TRY(force_at(c, q, c.w.U64, c.w.U32, phi, part, cg ? *cg : dummy, F, nullptr, 0.0));
+  SM_TRY(force_at(c, q, c.w.U64, c.w.U32, phi, part, cg ? *cg : dummy, F, nullptr, 0.0,
+                  part == SM_PART_HEAVY ? phi : nullptr));
   return c.sync();
 }
 
@@ -337,14 +451,15 @@ int sm_fg_shifted_force(const sm_lattice* lat, const double* q, const double* ph
                         sm_stats* stats, void* stream) {
   Ctx c;
   SM_TRY(c.init(lat, ws, ws_bytes, stream, stats));
-  SM_TRY(check_part(part));
+  SM_TRY(check_split_part(lat, part));
   SM_TRY(check_cg(cg));
   SM_TRY(fields_ok({q, F}, "sm_fg_shifted_force"));
-  if (part & SM_PART_FERMION) {
+  if (part & ~SM_PART_GAUGE) {
     SM_TRY(fields_ok({phi}, "sm_fg_shifted_force"));
     SM_TRY(make_links(c, q, c.w.U64, c.w.U32, *cg));
   }
-  SM_TRY(shifted_force(c, q, c.w.U64, c.w.U32, phi, part, h, *cg, F, nullptr, 0.0));
+  SM_TRY(shifted_force(c, q, c.w.U64, c.w.U32, phi, part, h, *cg, F, nullptr, 0.0,
+                       part == SM_PART_HEAVY ? phi : nullptr));
   return c.sync();
 }
 
@@ -353,11 +468,13 @@ int sm_force_gradient(const sm_lattice* lat, const double* q, const double* phi,
                       sm_stats* stats, void* stream) {
   Ctx c;
   SM_TRY(c.init(lat, ws, ws_bytes, stream, stats));
-  SM_TRY(check_part(part));
+  if (part == SM_PART_HEAVY)
+    return fail(SM_ERR_ARG, "sm_force_gradient: no force-gradient term of the heavy part");
+  SM_TRY(check_split_part(lat, part));
   SM_TRY(check_cg(cg));
   SM_TRY(fields_ok({q, C}, "sm_force_gradient"));
   if (F && !al16(F)) return fail(SM_ERR_ARG, "sm_force_gradient: F not aligned");
-  if (part & SM_PART_FERMION) {
+  if (part & ~SM_PART_GAUGE) {
     SM_TRY(fields_ok({phi}, "sm_force_gradient"));
     SM_TRY(make_links(c, q, c.w.U64, c.w.U32, *cg));
   }
@@ -407,7 +524,7 @@ int sm_md_trajectory(const sm_lattice* lat, double* q, double* p, const double* 
                      void* stream) {
   Ctx c;
   SM_TRY(c.init(lat, ws, ws_bytes, stream, stats));
-  SM_TRY(check_md(md));
+  SM_TRY(check_md(md, lat));
   if (md->n < 1 || !(md->tau > 0)) return fail(SM_ERR_ARG, "md: n >= 1 and tau > 0 required");
   SM_TRY(fields_ok({q, p, phi}, "sm_md_trajectory"));
   c.strict = false;
@@ -421,7 +538,7 @@ int sm_md_step(const sm_lattice* lat, double* q, double* p, const double* phi,
                void* stream) {
   Ctx c;
   SM_TRY(c.init(lat, ws, ws_bytes, stream, stats));
-  SM_TRY(check_md(md));
+  SM_TRY(check_md(md, lat));
   SM_TRY(fields_ok({q, p, phi}, "sm_md_step"));
   c.strict = false;
   SM_TRY(md_run(c, q, p, phi, *md, h, 1));
@@ -433,10 +550,26 @@ int sm_md_step(const sm_lattice* lat, double* q, double* p, const double* phi,
 
 namespace sm {
 
+// S_h + S_r of the split action at the links in c.w.U64/U32 into Sr[nchains]
+// (with the kinetic term and S_G when p, q are given) and Sh[nchains].
+static int split_energies(Ctx& c, const double* q, const double* p, const sm_cg_params& cgH,
+                          double* K, double* SG, double* Sr, double* Sh) {
+  Ctx h = heavy_ctx(c);
+  SM_TRY(launch_dslash<double>(h, c.w.U64, c.w.phi, c.w.psi, true, nullptr, 0.0));
+  SM_TRY(cg_solve(c, c.w.U64, c.w.U32, c.w.psi, c.w.xi, cgH, nullptr, nullptr));
+  SM_TRY(launch_energies(c, q, p, c.w.psi, c.w.xi, K, SG, Sr));
+  const int rc = cg_solve(h, c.w.U64, c.w.U32, c.w.phi_h, c.w.xi, cgH, nullptr, nullptr);
+  merge_flags(c, h);
+  if (rc) return rc;
+  return launch_energies(c, nullptr, nullptr, c.w.phi_h, c.w.xi, nullptr, nullptr, Sh);
+}
+
 // The device part of one HMC update of every chain (Sec. 2.1): heatbath
 // phi = D^dag eta, H at the start, the MD trajectory, H at the end.  Enqueues
 // only (no host synchronisation when c.deferred).  Energies land in
-// c.w.out = [K0, SG0, SF0, K1, SG1, SF1][nchains].
+// c.w.out = [K0, SG0, SF0, K1, SG1, SF1, Sh0, Sh1][nchains]: SF the fermion
+// action (the ratio part S_r for the three-level schemes), Sh the heavy part
+// S_h (zero without the split).
 static int hmc_enqueue(Ctx& c, double* q, const double* p0, const double* eta,
                        const sm_md_params& md) {
   const int nc = c.L->nchains;
@@ -447,6 +580,34 @@ static int hmc_enqueue(Ctx& c, double* q, const double* p0, const double* eta,
   double* out = c.w.out;
   if (c.deferred) SM_CU(cudaMemsetAsync(c.w.acc, 0, 3 * sizeof(int) * nc, c.s));
   SM_TRY(make_links(c, q, c.w.U64, c.w.U32, cg));
+  if (three_level(md.scheme)) {
+    // phi_h = D_h^dag eta_h; phi_r = D_h^dag^{-1} D^dag eta_r = D_h (D_h^dag D_h)^{-1} D^dag eta_r
+    const double* eta_r = eta;
+    const double* eta_h = eta + 4 * (size_t)c.L->N;
+    Ctx h = heavy_ctx(c);
+    SM_TRY(launch_dslash<double>(h, c.w.U64, eta_h, c.w.phi_h, true, nullptr, 0.0));
+    SM_TRY(launch_dslash<double>(c, c.w.U64, eta_r, c.w.b, true, nullptr, 0.0));
+    bool have = false;
+    int rc = cg_solve(h, c.w.U64, c.w.U32, c.w.b, c.w.xi, cg, nullptr, nullptr, c.w.phi, &have);
+    merge_flags(c, h);
+    if (rc) return rc;
+    c.st->inversions += 1;
+    if (!have) SM_TRY(launch_dslash<double>(h, c.w.U64, c.w.xi, c.w.phi, false, nullptr, 0.0));
+    SM_CU(cudaMemcpyAsync(c.w.qsave, q, lbytes, cudaMemcpyDeviceToDevice, c.s));
+    SM_CU(cudaMemcpyAsync(c.w.pw, p0, lbytes, cudaMemcpyDeviceToDevice, c.s));
+    if (md.sf_start == SM_SF_NOISE) {
+      // S_r = eta_r^dag eta_r, S_h = eta_h^dag eta_h for the pseudofermions above
+      SM_TRY(launch_energies(c, q, c.w.pw, eta_r, eta_r, out, out + nc, out + 2 * nc));
+      SM_TRY(launch_energies(c, nullptr, nullptr, eta_h, eta_h, nullptr, nullptr, out + 6 * nc));
+    } else {
+      SM_TRY(split_energies(c, q, c.w.pw, cgH, out, out + nc, out + 2 * nc, out + 6 * nc));
+    }
+    SM_TRY(md_run(c, q, c.w.pw, c.w.phi, md, md.tau / md.n, md.n, c.w.phi_h));
+    SM_TRY(make_links(c, q, c.w.U64, c.w.U32, cg));
+    return split_energies(c, q, c.w.pw, cgH, out + 3 * nc, out + 4 * nc, out + 5 * nc,
+                          out + 7 * nc);
+  }
+  SM_CU(cudaMemsetAsync(out + 6 * nc, 0, 2 * sizeof(double) * nc, c.s));
   SM_TRY(launch_dslash<double>(c, c.w.U64, eta, c.w.phi, true, nullptr, 0.0));
   SM_CU(cudaMemcpyAsync(c.w.qsave, q, lbytes, cudaMemcpyDeviceToDevice, c.s));
   SM_CU(cudaMemcpyAsync(c.w.pw, p0, lbytes, cudaMemcpyDeviceToDevice, c.s));
@@ -469,7 +630,7 @@ static int hmc_finish(Ctx& c, double* q, const double* u, double* dH, double* H0
                       double* p_out, double* q_md) {
   const int nc = c.L->nchains;
   const size_t lbytes = sizeof(double) * 2 * (size_t)c.L->N;
-  std::vector<double> h(6 * (size_t)nc);
+  std::vector<double> h(8 * (size_t)nc);
   std::vector<int> acc(3 * (size_t)nc, 0);
   SM_CU(cudaMemcpyAsync(h.data(), c.w.out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c.s));
   if (c.deferred)
@@ -488,8 +649,8 @@ static int hmc_finish(Ctx& c, double* q, const double* u, double* dH, double* H0
   std::vector<int> reject(nc);
   bool any_nan = false, any_reject = false;
   for (int i = 0; i < nc; ++i) {
-    const double h0 = h[i] + h[nc + i] + h[2 * nc + i];
-    const double h1 = h[3 * nc + i] + h[4 * nc + i] + h[5 * nc + i];
+    const double h0 = h[i] + h[nc + i] + h[2 * nc + i] + h[6 * nc + i];
+    const double h1 = h[3 * nc + i] + h[4 * nc + i] + h[5 * nc + i] + h[7 * nc + i];
     const double d = h1 - h0;
     dH[i] = d;
     if (H0) H0[i] = h0;
@@ -538,7 +699,7 @@ int sm_hmc_trajectory(const sm_lattice* lat, double* q, const double* p0, const 
                       sm_stats* stats, void* stream) {
   Ctx c;
   SM_TRY(c.init(lat, ws, ws_bytes, stream, stats));
-  SM_TRY(check_md(md));
+  SM_TRY(check_md(md, lat));
   if (md->n < 1 || !(md->tau > 0)) return fail(SM_ERR_ARG, "md: n >= 1 and tau > 0 required");
   SM_TRY(fields_ok({q, p0, eta}, "sm_hmc_trajectory"));
   if (!u || !dH || !accepted) return fail(SM_ERR_ARG, "sm_hmc_trajectory: NULL host output");
@@ -558,7 +719,7 @@ int sm_hmc_graph_create(const sm_lattice* lat, double* q, const double* p0, cons
   if (!stream) return fail(SM_ERR_ARG, "sm_hmc_graph_create: needs a non-default stream");
   Ctx c;
   SM_TRY(c.init(lat, ws, ws_bytes, stream, nullptr));
-  SM_TRY(check_md(md));
+  SM_TRY(check_md(md, lat));
   if (md->n < 1 || !(md->tau > 0)) return fail(SM_ERR_ARG, "md: n >= 1 and tau > 0 required");
   SM_TRY(fields_ok({q, p0, eta}, "sm_hmc_graph_create"));
   if (!all_chain_resident(lat, *md))

@@ -91,15 +91,18 @@ def test_binding_constants_match_the_header():
     names = {"leapfrog": "SM_LEAPFROG", "five_stage": "SM_FIVE_STAGE",
              "five_stage_fg": "SM_FIVE_STAGE_FG", "nested_leapfrog": "SM_NESTED_LEAPFROG",
              "nested_five_stage": "SM_NESTED_FIVE_STAGE", "nested_fg": "SM_NESTED_FG",
-             "adapted_nested_fg": "SM_ADAPTED_NESTED_FG", "eleven_stage": "SM_ELEVEN_STAGE"}
+             "adapted_nested_fg": "SM_ADAPTED_NESTED_FG", "eleven_stage": "SM_ELEVEN_STAGE",
+             "nested3_leapfrog": "SM_NESTED3_LEAPFROG",
+             "adapted_nested3_fg": "SM_ADAPTED_NESTED3_FG"}
     assert set(B.SCHEMES) == set(names)
     for k, v in B.SCHEMES.items():
         assert v == d[names[k]], k
     for k in ("SM_OK", "SM_ERR_ARG", "SM_ERR_CUDA", "SM_ERR_NOT_CONVERGED", "SM_ERR_TIMEOUT",
               "SM_ERR_NAN", "SM_F64", "SM_F32", "SM_MIXED"):
         assert getattr(B, k) == d[k], k
-    assert (B.PART_GAUGE, B.PART_FERMION, B.PART_FULL) == (
-        d["SM_PART_GAUGE"], d["SM_PART_FERMION"], d["SM_PART_FULL"])
+    assert (B.PART_GAUGE, B.PART_FERMION, B.PART_FULL, B.PART_HEAVY, B.PART_RATIO) == (
+        d["SM_PART_GAUGE"], d["SM_PART_FERMION"], d["SM_PART_FULL"], d["SM_PART_HEAVY"],
+        d["SM_PART_RATIO"])
     assert (B.FG_EXACT, B.FG_SHIFTED) == (d["SM_FG_EXACT"], d["SM_FG_SHIFTED"])
     assert B.CG_VARIANTS == d["SM_CG_VARIANTS"]
 
