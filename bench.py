@@ -1028,6 +1028,9 @@ PAPER = {
                ("eleven_stage", "exact", 0.0625, 12, 384)],
     # |Delta H| against h (Fig. 1) for every integrator
     "scan_h": (0.0125, 0.025, 0.05, 0.1),
+    # the three-level adapted scheme: heavy mass shifts and heavy steps per
+    # middle block tried
+    "heavy_dm": (0.2, 0.5, 1.0), "M2": (1, 2),
     "scan": [("leapfrog", "exact"), ("nested_leapfrog", "exact"), ("five_stage", "exact"),
              ("nested_five_stage", "exact"), ("five_stage_fg", "exact"),
              ("five_stage_fg", "shifted"), ("nested_fg", "exact"), ("adapted_nested_fg", "exact"),
@@ -1106,10 +1109,12 @@ def run_paper(args):
                 "mean_abs_dH_all": float(a.mean()),
                 "inversions_per_traj_md": int(st["inversions"])}
 
-    def measure_n(scheme, fg, n, draws):
+    def measure_n(scheme, fg, n, draws, M=Wp["M"], M2=1):
         """Acceptance and inversions at n steps on fixed draws (the same
-        momenta and noise for every n of one integrator)."""
-        md = P.MD(scheme=scheme, tau=Wp["tau"], n=n, M=Wp["M"], fg=fg, cg=cg, tol_action=1e-12,
+        momenta and noise for every n of one integrator); the CG iterations
+        of the trajectory (all its solves, H included) per chain are its
+        cost."""
+        md = P.MD(scheme=scheme, tau=Wp["tau"], n=n, M=M, M2=M2, fg=fg, cg=cg, tol_action=1e-12,
                   merge_kicks=False)
         p, e, u = draws
         q = qb.clone()
@@ -1118,20 +1123,25 @@ def run_paper(args):
         ok = np.isfinite(dH)
         return {"n": n, "h": round(Wp["tau"] / n, 6), "acceptance": float(np.mean(acc)),
                 "acceptance_expected": float(np.mean(np.exp(np.minimum(0.0, -dH[ok]))) * ok.mean()),
-                "inversions_per_traj_md": int(st["inversions"])}
+                "inversions_per_traj_md": int(st["inversions"]),
+                "cg_iterations_per_traj": round(st["chain_iterations"] / B, 1)}
 
-    def h_at_90(scheme, fg, h_paper):
+    def h_at_90(scheme, fg, h_paper, M=Wp["M"], M2=1):
         """The step size at 90 % acceptance: the smallest n = tau / h whose
         expected acceptance <min(1, e^-dH)> over the 200 momentum sets is at
         least 0.9, found by bracketing from the paper's h and bisecting over
         integer n on one fixed set of draws; h90 interpolated linearly in h
         between the bracketing n."""
         draws = draw(B, B * L * T)
+        if scheme in ("nested3_leapfrog", "adapted_nested3_fg"):
+            p3, e3, u3 = draws
+            _, e_h, _ = draw(B, B * L * T)
+            draws = (p3, torch.cat([e3, e_h]), u3)
         seen = {}
 
         def A(n):
             if n not in seen:
-                seen[n] = measure_n(scheme, fg, n, draws)
+                seen[n] = measure_n(scheme, fg, n, draws, M, M2)
             return seen[n]["acceptance_expected"]
 
         n0 = max(2, int(math.ceil(Wp["tau"] / h_paper - 1e-9)))
@@ -1162,6 +1172,7 @@ def run_paper(args):
                 "acceptance_expected_at_n": round(a_hi, 4),
                 "acceptance_at_n": round(r["acceptance"], 4),
                 "inversions_per_traj_md_at_n": r["inversions_per_traj_md"],
+                "cg_iterations_per_traj_at_n": r["cg_iterations_per_traj"],
                 "evaluated": sorted(({"n": k, "acceptance_expected": round(v["acceptance_expected"], 4)}
                                      for k, v in seen.items()), key=lambda d: d["n"])}
 
@@ -1181,13 +1192,35 @@ def run_paper(args):
         log(f"paper table1 {scheme}/{fg} h={r['h']}: acc {r['acceptance']} median |dH| "
             f"{r['median_abs_dH']:.4g} unstable {r['unstable']} inversions "
             f"{r['inversions_per_traj_md']}")
+    # the outlook of the paper's Conclusions: the determinant split over two
+    # masses, three time scales, the force-gradient term for the ratio part
+    # only; each variant at its own 90 % step size, its cost in CG iterations
+    # per trajectory beside the two-level adapted scheme's
+    three = None
+    if not args.no_h90 and not args.no_three_level:
+        base = next(r["at_90_percent"] for r in table if r["scheme"] == "adapted_nested_fg")
+        three = {"two_level_adapted_nested_fg": {
+            "h90": base["h90"], "n": base["n"],
+            "cg_iterations_per_traj": base["cg_iterations_per_traj_at_n"],
+            "inversions_per_traj_md": base["inversions_per_traj_md_at_n"]}, "variants": []}
+        for dm in Wp["heavy_dm"]:
+            lat.set_heavy(dm)
+            for M2 in Wp["M2"]:
+                M = max(1, int(math.ceil(Wp["M"] / M2)))  # the gauge micro step ~ h/10
+                r = h_at_90("adapted_nested3_fg", "exact", 0.056, M=M, M2=M2)
+                r.update({"dm": dm, "M2": M2, "M": M})
+                three["variants"].append(r)
+                log(f"paper three-level dm={dm} M2={M2} M={M}: h90 {r['h90']} cg iters/traj "
+                    f"{r['cg_iterations_per_traj_at_n']} (two-level "
+                    f"{base['cg_iterations_per_traj_at_n']})")
     scan = []
     for scheme, fg in Wp["scan"]:
         for h in Wp["scan_h"]:
             scan.append(measure(scheme, fg, h))
     dt = time.time() - t1
     ntraj = B * (len(table) + len(scan) + sum(len(r.get("at_90_percent", {}).get("evaluated", []))
-                                             for r in table))
+                                             for r in table)
+                 + (sum(len(v["evaluated"]) for v in three["variants"]) if three else 0))
     res = {
         "metric": "paper workload: trajectories/s over the Table 1 and Fig. 1 runs",
         "value": round(ntraj / dt, 3), "unit": "trajectories/s", "n_gpus": 1,
@@ -1202,7 +1235,7 @@ def run_paper(args):
         "inversions_counting": "D^-1 per trajectory in the MD (one D^dag D solve = 2; the "
                                "two solves of H are not counted); Table 1 rows with every kick "
                                "evaluated (as the paper counts), plus the merged-kick count",
-        "table1": table, "scan": scan}
+        "table1": table, "scan": scan, "three_level": three}
     if args.out:
         with open(args.out, "w") as f:
             f.write(json.dumps(res, indent=1) + "\n")
@@ -1502,6 +1535,8 @@ def main():
     ap.add_argument("--out", default=None, help="also write the JSON result to this file")
     ap.add_argument("--therm-paper", type=int, default=150,
                     help="thermalisation trajectories of the paper workload")
+    ap.add_argument("--no-three-level", action="store_true",
+                    help="paper workload: skip the three-level (determinant split) variants")
     ap.add_argument("--no-h90", action="store_true",
                     help="paper workload: skip the search for the 90 %% acceptance step size")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])

@@ -591,7 +591,6 @@ static int hmc_enqueue(Ctx& c, double* q, const double* p0, const double* eta,
     int rc = cg_solve(h, c.w.U64, c.w.U32, c.w.b, c.w.xi, cg, nullptr, nullptr, c.w.phi, &have);
     merge_flags(c, h);
     if (rc) return rc;
-    c.st->inversions += 1;
     if (!have) SM_TRY(launch_dslash<double>(h, c.w.U64, c.w.xi, c.w.phi, false, nullptr, 0.0));
     SM_CU(cudaMemcpyAsync(c.w.qsave, q, lbytes, cudaMemcpyDeviceToDevice, c.s));
     SM_CU(cudaMemcpyAsync(c.w.pw, p0, lbytes, cudaMemcpyDeviceToDevice, c.s));
