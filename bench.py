@@ -1274,6 +1274,11 @@ def measure_ddagd(torch, P, dev, reps=20, prec="f32", warmup=3, rates=None):
     # timed launch instead of inside it
     flush = torch.empty(int(256 * 2 ** 20), dtype=torch.uint8, device=dev)
     clean = torch.zeros(int(32 * 2 ** 20), dtype=torch.int64, device=dev)
+    tuned = None
+    if prec == "f32":
+        # the streaming form's strip height, picked by the library's autotuner
+        h, cand = lat.autotune_ddagd(*sets[0])
+        tuned = {"strip_height": h, "candidates_ms": [[a, round(b, 4)] for a, b in cand]}
     for i in range(warmup):
         U, psi, out = sets[i % 2]
         lat.apply_DdagD(U, psi, out)
@@ -1325,7 +1330,8 @@ def measure_ddagd(torch, P, dev, reps=20, prec="f32", warmup=3, rates=None):
                               "l2": "flushed and clean before each launch (write 256 MiB, then "
                                     "read 256 MiB); the launch's own dirty output is written "
                                     "back after its end event"},
-            "reps": reps, "traffic": ncu_traffic(kname) if prec == "f32" else None,
+            "reps": reps, "autotune": tuned,
+            "traffic": ncu_traffic(kname) if prec == "f32" else None,
             "traffic_unit": "DRAM bytes per launch (ncu, back-to-back launches, cache control "
                             "none)",
             **fp64_roofline(ms_b2b, L * T, prec, rates)}
@@ -1506,7 +1512,7 @@ def run_stencil(args):
                                    "kernel": f32["kernel"],
                                    "traffic": f32["traffic"],
                                    "traffic_unit": f32["traffic_unit"]},
-                      "single_launch": f32["single_launch"],
+                      "single_launch": f32["single_launch"], "autotune": f32["autotune"],
                       "f64": f64, "measured_rates": rates}), flush=True)
 
 

@@ -303,6 +303,25 @@ int sm_apply_DdagD(const sm_lattice* lat, const void* U, const void* in, void* o
 int sm_apply_DdagD_noalloc(int L, int T, double m0, const void* U, const void* in, void* out,
                            int prec, void* stream);
 
+/* Autotuner of the strip height of the streaming FP32 D^dag D (the form
+ * sm_apply_DdagD takes for batches of at least 2^18 sites whose chains are
+ * all wide enough: each warp walks a strip of 60 columns and `height` rows).
+ * Times, on the given operands (U32, in, out as for sm_apply_DdagD with
+ * SM_F32; out is overwritten), 10 launches back to back per candidate
+ * height -- the lowest heights whose blocks fit on the GPU in 1, 2, 3 and 4
+ * waves, and two and four times the one-wave height -- and keeps the fastest
+ * in the lattice object for later sm_apply_DdagD calls.  The one-wave height
+ * is the default before tuning.  height (host, may be NULL) receives the
+ * choice (0 if the streaming form does not serve this lattice: then nothing
+ * is timed), heights and ms (host [SM_DDAGD_HEIGHTS], may be NULL) each
+ * candidate and its time per launch, -1 past the last.  No counterpart in
+ * the paper: a tuning of the library's own tiling.  Allocates and frees the
+ * candidates' strip tables (a set-up call, not for the hot path);
+ * synchronises. */
+#define SM_DDAGD_HEIGHTS 8
+int sm_autotune_ddagd(sm_lattice* lat, const float* U32, const float* in, float* out,
+                      int* height, int* heights, double* ms, void* stream);
+
 /* -------------------------------------------------------- inversion ------- */
 
 /* Solves D^dag D x = b for every chain (Sec. 3: the inversions behind

@@ -41,6 +41,7 @@ SCHEMES = {
 THREE_LEVEL = ("nested3_leapfrog", "adapted_nested3_fg")
 FG_EXACT, FG_SHIFTED = 0, 1
 CG_VARIANTS = 8  # kernel variants of the chain-resident mixed CG (SM_CG_VARIANTS)
+DDAGD_HEIGHTS = 8  # candidate strip heights of the streaming D^dag D (SM_DDAGD_HEIGHTS)
 PART_HEAVY, PART_RATIO = 4, 8
 PARTS = {"gauge": PART_GAUGE, "fermion": PART_FERMION, "full": PART_FULL, "heavy": PART_HEAVY,
          "ratio": PART_RATIO}
@@ -110,6 +111,7 @@ _SIGS = {
     "sm_autotune_cg": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(CgParams), _P,
                                       ctypes.c_size_t, _P, _P, _P]),
     "sm_set_cg_variant": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sm_autotune_ddagd": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "sm_gauge_force": (ctypes.c_int, [_P, _P, _P, _P]),
     "sm_fermion_force": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(CgParams), _P, _P,
                                         ctypes.c_size_t, ctypes.POINTER(Stats), _P]),
@@ -324,6 +326,19 @@ class Lattice:
                                    ctypes.byref(p), *self._ws(), ctypes.byref(v), ms.ctypes.data,
                                    _stream()))
         return v.value, ms.tolist()
+
+    def autotune_ddagd(self, U32, psi32, out=None):
+        """Times the streaming D^dag D's candidate strip heights on these
+        FP32 operands and keeps the fastest (sm_autotune_ddagd); returns
+        (height, [(candidate height, ms per launch)]); height 0 when the
+        streaming form does not serve this lattice."""
+        out = torch.empty_like(psi32) if out is None else out
+        h = ctypes.c_int()
+        hs = np.zeros(DDAGD_HEIGHTS, dtype=np.int32)
+        ms = np.zeros(DDAGD_HEIGHTS)
+        _check(_LIB.sm_autotune_ddagd(self._h, _ptr(U32), _ptr(psi32), _ptr(out), ctypes.byref(h),
+                                      hs.ctypes.data, ms.ctypes.data, _stream()))
+        return h.value, [(int(a), float(b)) for a, b in zip(hs, ms) if a > 0]
 
     def hmc_graph(self, q, p0, eta, md: MD, stream=None) -> "HmcGraph":
         """Captures one HMC trajectory of every chain as a CUDA graph bound to

@@ -226,6 +226,24 @@ static int make_strips(const sm_lattice* lat, int TT, int4** d) {
   return SM_OK;
 }
 
+// Candidate strip heights of the streaming D^dag D for this lattice: the
+// lowest heights whose blocks fit on the GPU in 1, 2, 3 and 4 waves, and two
+// and four times the one-wave height (taller strips: fewer halo re-reads,
+// fewer blocks), at most the tallest chain, each once, ascending.
+static std::vector<int> stream_candidates(const sm_lattice* lat, int nsm, int occ) {
+  int tmax = 0;
+  for (const ChainInfo& ci : lat->chains) tmax = std::max(tmax, ci.T);
+  std::vector<int> c;
+  for (int w = 1; w <= 4; ++w) c.push_back(stream_height(lat, nsm, occ * w));
+  const int t1 = c[0];
+  c.push_back(2 * t1);
+  c.push_back(4 * t1);
+  for (int& v : c) v = std::max(8, std::min(v, std::max(8, tmax)));
+  std::sort(c.begin(), c.end());
+  c.erase(std::unique(c.begin(), c.end()), c.end());
+  return c;
+}
+
 static int build_stream_table(sm_lattice* lat) {
   if (!lat->stream_ok) return SM_OK;
   const int rc = make_strips(lat, lat->stream_tt, &lat->d_stream);
@@ -327,3 +345,76 @@ template int launch_ddagd<float>(Ctx&, const float*, const float*, float*);
 template int launch_ddagd<double>(Ctx&, const double*, const double*, double*);
 
 }  // namespace sm
+
+using namespace sm;
+
+extern "C" int sm_autotune_ddagd(sm_lattice* lat, const float* U32, const float* in, float* out,
+                                 int* height, int* heights, double* ms, void* stream) {
+  if (!lat || !U32 || !in || !out) return fail(SM_ERR_ARG, "sm_autotune_ddagd: NULL argument");
+  if ((((uintptr_t)U32) | ((uintptr_t)in) | ((uintptr_t)out)) & 15)
+    return fail(SM_ERR_ARG, "sm_autotune_ddagd: unaligned field");
+  if (in == out) return fail(SM_ERR_ARG, "sm_autotune_ddagd: in and out alias");
+  if (heights)
+    for (int k = 0; k < SM_DDAGD_HEIGHTS; ++k) heights[k] = -1;
+  if (ms)
+    for (int k = 0; k < SM_DDAGD_HEIGHTS; ++k) ms[k] = -1.0;
+  if (!lat->stream_ok) {
+    if (height) *height = 0;  // the tiled forms serve this lattice: nothing to tune
+    return SM_OK;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int nsm = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, lat->device);
+  if (e != cudaSuccess) return fail(SM_ERR_CUDA, "sm_autotune_ddagd: %s", cudaGetErrorString(e));
+  const std::vector<int> cand = stream_candidates(lat, nsm, ddagd_stream_occupancy());
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return fail(SM_ERR_CUDA, "sm_autotune_ddagd: %s", cudaGetErrorString(e));
+  const int reps = 10;
+  int best = lat->stream_tt;
+  float best_ms = -1.f;
+  int rc = SM_OK;
+  for (size_t k = 0; k < cand.size() && k < (size_t)SM_DDAGD_HEIGHTS && rc == SM_OK; ++k) {
+    const int TT = cand[k];
+    int4* table = nullptr;
+    if ((rc = make_strips(lat, TT, &table))) break;
+    const unsigned nb = (unsigned)stream_blocks(lat, TT);
+    for (int r = 0; r < 2; ++r)  // warm-up
+      k_ddagd_stream<<<nb, kSThreads, 0, s>>>(lat->d_chains, table, TT, U32, in, out);
+    e = cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r)
+      k_ddagd_stream<<<nb, kSThreads, 0, s>>>(lat->d_chains, table, TT, U32, in, out);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaFree(table);
+    if (e != cudaSuccess) {
+      rc = fail(SM_ERR_CUDA, "sm_autotune_ddagd: %s", cudaGetErrorString(e));
+      break;
+    }
+    add_launches(reps + 2);
+    t /= reps;
+    if (heights) heights[k] = TT;
+    if (ms) ms[k] = t;
+    if (best_ms < 0.f || t < best_ms) {
+      best_ms = t;
+      best = TT;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (best != lat->stream_tt) {
+    int4* table = nullptr;
+    if ((rc = make_strips(lat, best, &table))) return rc;
+    cudaFree(lat->d_stream);
+    lat->d_stream = table;
+    lat->stream_tt = best;
+    lat->nstream = (int)stream_blocks(lat, best);
+  }
+  if (height) *height = lat->stream_tt;
+  return SM_OK;
+}

@@ -105,6 +105,7 @@ def test_binding_constants_match_the_header():
         d["SM_PART_RATIO"])
     assert (B.FG_EXACT, B.FG_SHIFTED) == (d["SM_FG_EXACT"], d["SM_FG_SHIFTED"])
     assert B.CG_VARIANTS == d["SM_CG_VARIANTS"]
+    assert B.DDAGD_HEIGHTS == d["SM_DDAGD_HEIGHTS"]
 
 
 def test_noalloc_binding_refuses_mismatched_tensors_before_launching():

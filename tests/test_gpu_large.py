@@ -232,3 +232,30 @@ def test_tma_wait_give_up_is_reported_and_recovers(torch):
     olat = sw.Lattice(L, T, 2.0, m0)
     ref = sw.apply_DdagD(olat, sw.links(q.reshape(T, L, 2)), psi.reshape(T, L, 2))
     assert rel_err(out, ref) < 4e-6
+
+
+def test_stencil_strip_height_autotuner(torch):
+    """sm_autotune_ddagd on a 512 x 512 lattice (the streaming form): it times
+    its candidate heights, keeps one of them, and sm_apply_DdagD with the
+    chosen height still matches the oracle; a lattice too small for the
+    streaming form reports height 0 and times nothing."""
+    import paper_1512_03812_gb300 as P
+    L = T = 512
+    m0 = sw.kappa_to_m0(0.24)
+    lat = P.Lattice(L, T, 2.0, m0)
+    q = I.hot_links(L, T, 95)
+    psi = I.spinor(L, T, 96)
+    U64, U32 = lat.links(torch.tensor(q, device="cuda"))
+    p32 = torch.tensor(psi, device="cuda").to(torch.complex64)
+    h, cand = lat.autotune_ddagd(U32, p32)
+    hs = [c[0] for c in cand]
+    assert h in hs and len(hs) >= 2 and hs == sorted(hs) and all(t > 0 for _, t in cand)
+    assert min(cand, key=lambda c: c[1])[0] == h
+    out = lat.apply_DdagD(U32, p32).cpu().numpy().reshape(T, L, 2)
+    olat = sw.Lattice(L, T, 2.0, m0)
+    ref = sw.apply_DdagD(olat, sw.links(q.reshape(T, L, 2)), psi.reshape(T, L, 2))
+    assert rel_err(out, ref) < 4e-6
+    small = P.Lattice(16, 16, 2.0, m0)
+    U64s, U32s = small.links(torch.zeros((256, 2), dtype=torch.float64, device="cuda"))
+    assert small.autotune_ddagd(U32s, torch.ones((256, 2), dtype=torch.complex64,
+                                                 device="cuda")) == (0, [])
