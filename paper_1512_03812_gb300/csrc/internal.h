@@ -3,6 +3,7 @@
 // kernel launchers.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -68,6 +69,15 @@ struct sm_lattice {
 };
 
 namespace sm {
+
+// An NVTX range over the object's lifetime: visible to Nsight tools (and to
+// ncu --nvtx-include), a cheap no-op without one.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 // Sets the thread-local message and returns `code`.
 int fail(int code, const char* fmt, ...);

@@ -340,6 +340,19 @@ static int check_md(const sm_md_params* md, const sm_lattice* L = nullptr) {
   return check_cg(&md->cg);
 }
 
+// The NVTX name of an operation (one range per operation of a schedule).
+static const char* op_name(const Op& op) {
+  if (op.k == OP_DRIFT) return "md:drift";
+  const bool fg = op.k == OP_FG;
+  switch (op.part) {
+    case SM_PART_GAUGE: return fg ? "md:fg gauge" : "md:kick gauge";
+    case SM_PART_FERMION: return fg ? "md:fg fermion" : "md:kick fermion";
+    case SM_PART_HEAVY: return fg ? "md:fg heavy" : "md:kick heavy";
+    case SM_PART_RATIO: return fg ? "md:fg ratio" : "md:kick ratio";
+    default: return fg ? "md:fg full" : "md:kick full";
+  }
+}
+
 // Executes `ops` on (q, p).  Links are refreshed lazily, only before an
 // operation that needs the fermion force.
 static int execute(Ctx& c, const std::vector<Op>& ops, double* q, double* p, const double* phi,
@@ -347,6 +360,7 @@ static int execute(Ctx& c, const std::vector<Op>& ops, double* q, double* p, con
   bool links_ok = false;
   const sm_cg_params& cg = md.cg;
   for (const Op& op : ops) {
+    Range range(op_name(op));
     if ((op.k != OP_DRIFT) && (op.part & ~SM_PART_GAUGE) && !links_ok) {
       SM_TRY(make_links(c, q, c.w.U64, c.w.U32, cg));
       links_ok = true;
@@ -578,6 +592,7 @@ static int hmc_enqueue(Ctx& c, double* q, const double* p0, const double* eta,
   sm_cg_params cgH = cg;  // the S_F solves of H
   if (md.tol_action > 0.0) cgH.tol = md.tol_action;
   double* out = c.w.out;
+  Range range("hmc:trajectory");
   if (c.deferred) SM_CU(cudaMemsetAsync(c.w.acc, 0, 3 * sizeof(int) * nc, c.s));
   SM_TRY(make_links(c, q, c.w.U64, c.w.U32, cg));
   if (three_level(md.scheme)) {
@@ -627,6 +642,7 @@ static int hmc_enqueue(Ctx& c, double* q, const double* p0, const double* eta,
 // decisions and restores the links of rejected chains.  Synchronises.
 static int hmc_finish(Ctx& c, double* q, const double* u, double* dH, double* H0, int* accepted,
                       double* p_out, double* q_md) {
+  Range range("hmc:metropolis");
   const int nc = c.L->nchains;
   const size_t lbytes = sizeof(double) * 2 * (size_t)c.L->N;
   std::vector<double> h(8 * (size_t)nc);

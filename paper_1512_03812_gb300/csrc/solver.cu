@@ -425,6 +425,7 @@ static int run(Ctx& c, CgArgs<R>& a, CgArgs<float>& af, int chunk, int maxit, lo
 
 int cg_solve(Ctx& c, const double* U64, const float* U32, const double* b, double* x,
              const sm_cg_params& cg, int* iters, double* relres, double* dx, bool* have_dx) {
+  Range range("cg_solve");
   if (have_dx) *have_dx = false;
   if (!U64 || !b || !x) return fail(SM_ERR_ARG, "cg_solve: NULL field");
   if (!(cg.tol > 0.0) || cg.maxit < 1) return fail(SM_ERR_ARG, "cg_solve: bad tol or maxit");
