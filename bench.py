@@ -71,7 +71,17 @@ SMEM_BYTES_COLUMN = 2 * 16 + (4 * 16 + 8 + 16) + (3 * 16 + 8 + 16)
 SMEM_BYTES_CLUSTER = 14 * 16
 SMEM_BYTES_PAIR = 2 * 16 + (64 + 40 + 32) // 2 + (64 + 40) // 2
 SMEM_BYTES_BY_VARIANT = ([SMEM_BYTES_STRIDED] + [SMEM_BYTES_COLUMN] * 2 + [SMEM_BYTES_CLUSTER] * 2
-                         + [SMEM_BYTES_PAIR] * 3)
+                         + [SMEM_BYTES_PAIR] * 4)
+# What actually crosses shared memory per site-iteration where it differs
+# from the layout's count: column pairs with x in tensor memory (8) take the
+# thread's own p in D and its own t in D^dag from registers, so D reads the
+# two outer x-neighbours (32) and 5 link halves (40) and writes 2 (32) per
+# two sites, D^dag reads 2 neighbours and 5 link halves, the p update 32:
+# 120 B.  x moves between TMEM and registers once per iteration (32 B per
+# site, not through shared memory).  The roofline keeps the column pairs'
+# 152 B (the operands an iteration consumes from on-chip storage), so that
+# the variants compare.
+SMEM_TRAFFIC_BY_VARIANT = {8: 32 + (32 + 40 + 32) // 2 + (32 + 40) // 2}
 # Shared-memory bandwidth per SM and clock (32 banks x 4 B).
 SMEM_BYTES_PER_CLK_PER_SM = 128
 NUM_SMS = 152
@@ -112,7 +122,7 @@ def ncu_traffic(kernel):
 CHAIN_KERNELS = ["k_cg_chain_mixed<8,512>", "k_cg_chain_col<8,512>", "k_cg_chain_col<16,256>",
                  "k_cg_chain_cluster<8,256,2>", "k_cg_chain_cluster<4,512,2>",
                  "k_cg_chain_pair<4,512,64,64,1>", "k_cg_chain_pair<8,256,64,64,1>",
-                 "k_cg_chain_pair<8,128,64,64,2>"]
+                 "k_cg_chain_pair<8,128,64,64,2>", "k_cg_chain_pair<8,256,64,64,1,true>"]
 
 
 def kappa_to_m0(k):
@@ -384,7 +394,8 @@ def run_ours(args):
                 "variants": ["strided 512x8", "column 512x8", "column 256x16",
                              "column 2-block cluster 256x8", "column 2-block cluster 512x4",
                              "column pairs 512x2x4", "column pairs 256x2x8",
-                             "column pairs 2-block cluster 128x2x8"]}
+                             "column pairs 2-block cluster 128x2x8",
+                             "column pairs 256x2x8, x in TMEM"]}
         log(f"autotuned chain CG: variant {v}, ms {vms}")
         del U64s, U32s, b_t
 
@@ -592,6 +603,7 @@ def run_ours(args):
                     "peak_nominal_source": f"{NUM_SMS} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x "
                                            f"{f_mhz:.0f} MHz (median SM clock under load)",
                     "bytes_per_site_iter": sbytes,
+                    "smem_bytes_per_site_iter": SMEM_TRAFFIC_BY_VARIANT.get(var, sbytes),
                     "traffic": ncu_traffic(kname), "traffic_unit": "DRAM bytes per launch (ncu)",
                     "hbm_equivalent": {"achieved": round(hbm_eq, 1), "peak": hbm,
                                        "unit": "GB/s", "frac": round(hbm_eq / hbm, 4),

@@ -116,7 +116,7 @@ typedef struct sm_lattice sm_lattice;
 #define SM_CG_CHAIN 2  /* one thread block owns one chain's whole solve; FP32 fields in
                           shared memory (chains of at most 4096 sites for SM_MIXED,
                           16384 for SM_F64) */
-#define SM_CG_VARIANTS 8  /* kernel variants of the chain-resident mixed CG (sm_autotune_cg) */
+#define SM_CG_VARIANTS 9  /* kernel variants of the chain-resident mixed CG (sm_autotune_cg) */
 
 /* CG parameters.  The solve of D^dag D x = b starts from x = 0 and stops, per
  * chain, when |b - D^dag D x| <= tol |b|: for SM_F64 the recursive residual
@@ -343,7 +343,11 @@ int sm_cg_solve(const sm_lattice* lat, const double* U64, const float* U32, cons
  * distributed shared memory; 4: the same with 512 threads x 4 rows, one
  * block per SM; 5: column pairs, 512 threads x 2 columns x 4 rows of 64 x 64
  * chains; 6: column pairs, 256 threads x 2 columns x 8 rows; 7: column pairs
- * split over a cluster of two blocks, 128 threads x 2 columns x 8 rows each)
+ * split over a cluster of two blocks, 128 threads x 2 columns x 8 rows each;
+ * 8: variant 6 with the FP32 iterate x in tensor memory (TMEM, 128 columns
+ * per block, allocated and freed by the kernel) and, in the registers x
+ * leaves free, each thread's own p through the D walk and own t = D p
+ * through the D^dag walk; the arithmetic of 6 in the same order)
  * on the given solve (b, FP64; x is overwritten), and stores the fastest in the
  * lattice object, which later SM_MIXED chain-resident solves use.  variant
  * (host, may be NULL) receives the choice, ms (host [SM_CG_VARIANTS], may be

@@ -40,7 +40,7 @@ SCHEMES = {
 }
 THREE_LEVEL = ("nested3_leapfrog", "adapted_nested3_fg")
 FG_EXACT, FG_SHIFTED = 0, 1
-CG_VARIANTS = 8  # kernel variants of the chain-resident mixed CG (SM_CG_VARIANTS)
+CG_VARIANTS = 9  # kernel variants of the chain-resident mixed CG (SM_CG_VARIANTS)
 DDAGD_HEIGHTS = 8  # candidate strip heights of the streaming D^dag D (SM_DDAGD_HEIGHTS)
 PART_HEAVY, PART_RATIO = 4, 8
 PARTS = {"gauge": PART_GAUGE, "fermion": PART_FERMION, "full": PART_FULL, "heavy": PART_HEAVY,

@@ -598,6 +598,63 @@ __device__ __forceinline__ unsigned krank() {
     return 0;
 }
 
+// Tensor memory (TMEM, 256 KB per SM beside the register file and shared
+// memory) as storage for per-thread data a kernel touches once per
+// iteration.  A warp reaches the 32 TMEM lanes of its quarter (warp % 4);
+// thread i of the warp holds lane 32 (warp % 4) + i, and each tcgen05.ld/st
+// below moves 16 consecutive 32-bit columns of that lane to or from 16
+// registers.  One warp allocates the columns of the block and frees them
+// before the block exits.
+__device__ __forceinline__ void tm_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tm_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};\n" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+      "r"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void tm_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
+// A block barrier that orders the tcgen05 operations around it.
+__device__ __forceinline__ void tm_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+// Allocates `ncols` columns (a power of two, 32 to 512) by warp 0 and
+// returns their base address in every thread; ends with a barrier.
+__device__ __forceinline__ uint32_t tm_alloc(uint32_t* slot, uint32_t ncols) {
+  if ((threadIdx.x >> 5) == 0) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(slot);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  tm_sync();
+  return *slot;
+}
+// Frees the columns (every thread of the block; ends after warp 0 frees).
+__device__ __forceinline__ void tm_free(uint32_t base, uint32_t ncols) {
+  tm_sync();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(base), "r"(ncols)
+                 : "memory");
+}
+
 // Column-pair layout for L x T chains (compile-time shape, L * T = 2 R NT K):
 // thread tid owns the two columns 2k and 2k + 1 (k = tid % (L/2)) of the R
 // rows t0 .. t0 + R - 1 (t0 = (tid / (L/2)) R) of its block's part of the
@@ -627,10 +684,26 @@ constexpr int pair_min_blocks() {
   return (K > 1 && 48 * L * T / K <= 116 * 1024) ? 2 : 1;
 }
 
-template <int R, int NT, int L, int T, int K>
+// TM (one block, whole warpgroups): the FP32 iterate x, touched once per
+// iteration (x += alpha p in the p update, and at a reliable update), lives
+// in tensor memory instead of registers (the thread's 2 R sites in 8 R
+// columns of its warp's lane quarter).  The registers it leaves free hold
+// the thread's own p from the p update through the D walk and its own
+// t = D p from the D walk through the D^dag walk, so neither walk reads the
+// thread's own sites from shared memory (120 instead of 152 bytes of shared
+// memory per site-iteration).  The arithmetic and its order are those of
+// TM = false: the results are bitwise the same.  Keeping p in registers
+// across the D^dag walk as well spilled 364 bytes and was 11 % slower.
+template <int R, int NT, int L, int T, int K, bool TM = false>
 __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_pair(ChainCgArgs a) {
   static_assert(L % 2 == 0 && T % K == 0 && L * T == 2 * R * NT * K,
                 "one thread per two columns of R rows");
+  static_assert(!TM || (K == 1 && NT % 128 == 0 && R % 2 == 0),
+                "TMEM form: one block, whole warpgroups, four sites per 16-column chunk");
+  // TMEM form: the thread's 2 R sites of x take 8 R columns; the warps of
+  // one quarter take consecutive column groups
+  constexpr int TMC = 8 * R, TMG = NT / 128;
+  constexpr uint32_t TMCOLS = TMC * TMG <= 32 ? 32 : (TMC * TMG <= 64 ? 64 : (TMC * TMG <= 128 ? 128 : (TMC * TMG <= 256 ? 256 : 512)));
   static_assert(NT % 32 == 0 && (T / K) % R == 0 && NT == (L / 2) * (T / K / R),
                 "whole warps; the threads tile the part's rows in strips of R");
   constexpr int H = T / K, V = H * L, HL = L / 2;  // rows and sites of a block's part
@@ -661,6 +734,12 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
   // of the odd site)
   const int qe = k, qo = HL + k, qm = HL + (k == 0 ? HL - 1 : k - 1), qp = k + 1 == HL ? 0 : k + 1;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ uint32_t tm_slot;
+  uint32_t tm_base = 0, taddr = 0;
+  if constexpr (TM) {
+    tm_base = tm_alloc(&tm_slot, TMCOLS);
+    taddr = tm_base + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(TMC * (w >> 2));
+  }
   // the rows below and above the thread's strip: offsets in the part that
   // holds them, which is the one below (above) for the strip at the bottom
   // (top) of the part
@@ -699,8 +778,10 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
     return s;
   };
 
-  // [2 j] the even site of row t0 + j, [2 j + 1] the odd one
-  Sp<float> rv[2 * R], xv[2 * R];
+  // [2 j] the even site of row t0 + j, [2 j + 1] the odd one.  The TMEM
+  // form keeps the thread's own p in registers (pv) and x in TMEM; the
+  // other form x in registers (xv) and p in shared memory only.
+  Sp<float> rv[2 * R], xv[TM ? 1 : 2 * R], pv[TM ? 2 * R : 1], tv[TM ? 2 * R : 1];
   double bbl = 0.0;
 #pragma unroll
   for (int i = 0; i < 2 * R; ++i) {
@@ -711,9 +792,18 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
     const Sp<double> bv = ld_sp(a.b, base + l);
     bbl += norm2(bv);
     rv[i] = to_flt(bv);
-    xv[i] = {{0.f, 0.f}, {0.f, 0.f}};
+    if constexpr (TM)
+      pv[i] = {{0.f, 0.f}, {0.f, 0.f}};
+    else
+      xv[i] = {{0.f, 0.f}, {0.f, 0.f}};
     ps[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     st_sp(a.x, base + l, Sp<double>{{0, 0}, {0, 0}});
+  }
+  if constexpr (TM) {
+    const uint32_t zero[16] = {};
+#pragma unroll
+    for (int ch = 0; ch < 2 * R / 4; ++ch) tm_st16(taddr + 16 * ch, zero);
+    tm_wait_st();
   }
   const double bb = tsumd(bbl);
   if (bb == 0.0)  // x = 0: D x, which the reliable updates otherwise leave in t64
@@ -729,8 +819,17 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
   // (D or D^dag) f on the thread's two columns, walking down its rows (fb,
   // fa: f of the parts below and above); emit(j, even, odd) receives the two
   // results of row t0 + j
-  auto walk = [&](const float4* f, const float4* fb, const float4* fa, auto dag, auto emit) {
+  auto walk = [&](const float4* f, const float4* fb, const float4* fa, auto dag, auto own,
+                  auto emit) {
     constexpr bool DAG = decltype(dag)::value;
+    // the thread's own sites of f: 0 read from shared memory, 1 pv, 2 tv
+    constexpr int OWN = decltype(own)::value;
+    auto ownv = [&](int i) -> Sp<float> {
+      if constexpr (OWN == 1)
+        return pv[i];
+      else
+        return tv[i];
+    };
     auto cx = [](float2 v) { return Cx<float>{v.x, v.y}; };
     const float4* fbr = (bot ? fb : f) + rb;
     const float2* ubr = (bot ? utsb : uts) + rb;
@@ -738,14 +837,26 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
     // the backward t-hops into row t0, then the rows' own hops
     Cx<float> ge = hop_tm<DAG, float>(cx(ubr[qe]), sp_of(fbr[qe]));
     Cx<float> go = hop_tm<DAG, float>(cx(ubr[qo]), sp_of(fbr[qo]));
-    Sp<float> fce = sp_of(f[t0 * L + qe]), fco = sp_of(f[t0 * L + qo]);
+    Sp<float> fce, fco;
+    if constexpr (OWN != 0) {
+      fce = ownv(0);
+      fco = ownv(1);
+    } else {
+      fce = sp_of(f[t0 * L + qe]);
+      fco = sp_of(f[t0 * L + qo]);
+    }
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const int row = (t0 + j) * L;
       Sp<float> fne, fno;  // the row above: the thread's next row, or the strip's row above
       if (j + 1 < R) {      // (an index, not a pointer select: fewer registers)
-        fne = sp_of(f[row + L + qe]);
-        fno = sp_of(f[row + L + qo]);
+        if constexpr (OWN != 0) {
+          fne = ownv(2 * (j + 1));
+          fno = ownv(2 * (j + 1) + 1);
+        } else {
+          fne = sp_of(f[row + L + qe]);
+          fno = sp_of(f[row + L + qo]);
+        }
       } else {
         fne = sp_of(far[qe]);
         fno = sp_of(far[qo]);
@@ -766,19 +877,50 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
 
   while (run) {
     // p = r + beta p, and the previous step's x += alpha p
+    if constexpr (TM) {
 #pragma unroll
-    for (int i = 0; i < 2 * R; ++i) {
-      const int row = (t0 + i / 2) * L, q = row + ((i & 1) ? qo : qe);
-      const Sp<float> po = sp_of(ps[q]);
-      xv[i] = xv[i] + alpha * po;
-      ps[q] = f4_of(rv[i] + beta * po);
+      for (int ch = 0; ch < 2 * R / 4; ++ch) {
+        uint32_t xr[16];
+        tm_ld16(taddr + 16 * ch, xr);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = 4 * ch + u;
+          const int row = (t0 + i / 2) * L, q = row + ((i & 1) ? qo : qe);
+          const Sp<float> po = sp_of(ps[q]);
+          const Sp<float> xs =
+              sp_of(make_float4(__uint_as_float(xr[4 * u]), __uint_as_float(xr[4 * u + 1]),
+                                __uint_as_float(xr[4 * u + 2]), __uint_as_float(xr[4 * u + 3]))) +
+              alpha * po;
+          xr[4 * u] = __float_as_uint(xs.a.re);
+          xr[4 * u + 1] = __float_as_uint(xs.a.im);
+          xr[4 * u + 2] = __float_as_uint(xs.b.re);
+          xr[4 * u + 3] = __float_as_uint(xs.b.im);
+          pv[i] = rv[i] + beta * po;
+          ps[q] = f4_of(pv[i]);
+        }
+        tm_st16(taddr + 16 * ch, xr);
+      }
+      tm_wait_st();
+    } else {
+#pragma unroll
+      for (int i = 0; i < 2 * R; ++i) {
+        const int row = (t0 + i / 2) * L, q = row + ((i & 1) ? qo : qe);
+        const Sp<float> po = sp_of(ps[q]);
+        xv[i] = xv[i] + alpha * po;
+        ps[q] = f4_of(rv[i] + beta * po);
+      }
     }
     ksync<K>();  // every part's p (and, the first time, U) is written
     float pap = 0.f;
-    walk(ps, psb, psa, std::false_type{}, [&](int j, const Sp<float>& te, const Sp<float>& to) {
+    walk(ps, psb, psa, std::false_type{}, std::integral_constant<int, TM ? 1 : 0>{},
+         [&](int j, const Sp<float>& te, const Sp<float>& to) {
       const int row = (t0 + j) * L;
       ts[row + qe] = f4_of(te);
       ts[row + qo] = f4_of(to);
+      if constexpr (TM) {
+        tv[2 * j] = te;
+        tv[2 * j + 1] = to;
+      }
       pap += norm2(te) + norm2(to);
     });
     const float papt = tsum(pap, 0);  // its barrier also publishes ts
@@ -788,7 +930,8 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
     }
     alpha = rr / papt;
     float rn2 = 0.f;
-    walk(ts, tsb, tsa, std::true_type{}, [&](int j, const Sp<float>& ae, const Sp<float>& ao) {
+    walk(ts, tsb, tsa, std::true_type{}, std::integral_constant<int, TM ? 2 : 0>{},
+         [&](int j, const Sp<float>& ae, const Sp<float>& ao) {
       rv[2 * j] = rv[2 * j] - alpha * ae;
       rv[2 * j + 1] = rv[2 * j + 1] - alpha * ao;
       rn2 += norm2(rv[2 * j]) + norm2(rv[2 * j + 1]);
@@ -805,13 +948,36 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
     rmax = fmaxf(rmax, rr);
     if (rr <= tol2bb || rr < delta2 * rmax || it >= a.maxit) {
       // reliable update: x_hi += x + alpha p, r = b - A x_hi in FP64
+      if constexpr (TM) {
 #pragma unroll
-      for (int i = 0; i < 2 * R; ++i) {
-        const int row = (t0 + i / 2) * L;
-        const long long n = base + row + 2 * k + (i & 1);
-        const Sp<float> xs = xv[i] + alpha * sp_of(ps[row + ((i & 1) ? qo : qe)]);
-        st_sp(a.x, n, ld_sp_cg(a.x, n) + to_dbl(xs));
-        xv[i] = {{0.f, 0.f}, {0.f, 0.f}};
+        for (int ch = 0; ch < 2 * R / 4; ++ch) {
+          uint32_t xr[16];
+          tm_ld16(taddr + 16 * ch, xr);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = 4 * ch + u;
+            const int row = (t0 + i / 2) * L;
+            const long long n = base + row + 2 * k + (i & 1);
+            const Sp<float> xs =
+                sp_of(make_float4(__uint_as_float(xr[4 * u]), __uint_as_float(xr[4 * u + 1]),
+                                  __uint_as_float(xr[4 * u + 2]),
+                                  __uint_as_float(xr[4 * u + 3]))) +
+                alpha * sp_of(ps[row + ((i & 1) ? qo : qe)]);
+            st_sp(a.x, n, ld_sp_cg(a.x, n) + to_dbl(xs));
+          }
+          const uint32_t zero[16] = {};
+          tm_st16(taddr + 16 * ch, zero);
+        }
+        tm_wait_st();
+      } else {
+#pragma unroll
+        for (int i = 0; i < 2 * R; ++i) {
+          const int row = (t0 + i / 2) * L;
+          const long long n = base + row + 2 * k + (i & 1);
+          const Sp<float> xs = xv[i] + alpha * sp_of(ps[row + ((i & 1) ? qo : qe)]);
+          st_sp(a.x, n, ld_sp_cg(a.x, n) + to_dbl(xs));
+          xv[i] = {{0.f, 0.f}, {0.f, 0.f}};
+        }
       }
       alpha = 0.f;
       ksync<K>();
@@ -881,6 +1047,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
     // ps and ts in this iteration precedes the barrier of the |r|^2 sum
   }
   if constexpr (K > 1) ksync<K>();  // no block leaves while another may read its shared memory
+  if constexpr (TM) tm_free(tm_base, TMCOLS);  // every thread is done with TMEM
   if (threadIdx.x == 0 && rank == 0) {
     CgChain* cc = a.cgc + c;
     cc->bb = bb;
@@ -1212,7 +1379,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_cg_chain_f64(ChainCgArgs a
 // chain's shape to match).
 bool chain_variant_applies(const sm_lattice* L, int v) {
   if (v == 0) return true;
-  if (v < 0 || v > 7) return false;
+  if (v < 0 || v > 8) return false;
   if (v >= 5) {
     // column pairs of 64 x 64 chains: 512 threads x 4 rows, 256 x 8, and
     // 2-block clusters of 128 x 8
@@ -1293,6 +1460,9 @@ int chain_cg_prepare(const sm_lattice* L, const sm_cg_params& cg) {
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_cg_chain_pair<8, 256, 64, 64, 1>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_chain_pair<8, 256, 64, 64, 1, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_cg_chain_pair<8, 128, 64, 64, 2>,
@@ -1540,7 +1710,7 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
       go(k_cg_chain_col<8, 512>, 512);
     } else if (v == 2) {
       go(k_cg_chain_col<16, 256>, 256);
-    } else if (v == 5 || v == 6) {
+    } else if (v == 5 || v == 6 || v == 8) {
       // one block per chain, the chains longest first (k_chain_order)
       const int n = L->nchains;
       ChainCgArgs ao = a;
@@ -1550,7 +1720,9 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
         if (rc) return rc;
         ao.list = c.w.order;
       }
-      auto kern = v == 5 ? k_cg_chain_pair<4, 512, 64, 64, 1> : k_cg_chain_pair<8, 256, 64, 64, 1>;
+      auto kern = v == 5   ? k_cg_chain_pair<4, 512, 64, 64, 1>
+                  : v == 6 ? k_cg_chain_pair<8, 256, 64, 64, 1>
+                           : k_cg_chain_pair<8, 256, 64, 64, 1, true>;
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e == cudaSuccess) kern<<<grid, dim3(v == 5 ? 512 : 256), smem, c.s>>>(ao);
     } else if (v == 7) {

@@ -61,16 +61,17 @@ def test_graph_needs_chain_resident_solves(torch):
         b.lat.hmc_graph(q, b.dev(b.p()), b.dev(b.eta()), md)
 
 
-def test_graph_equals_eager_longest_first(torch):
-    """160 chains of 64 x 64 on the column-pair kernel pinned (variant 6):
-    its launches take the chains in the order of their previous solve's
-    iteration counts, which changes between solves; the results do not
-    depend on it (graph and eager bitwise equal, and a chain's solution equal
-    to that of the same chain solved alone)."""
+@pytest.mark.parametrize("variant", [6, 8])
+def test_graph_equals_eager_longest_first(torch, variant):
+    """160 chains of 64 x 64 on a column-pair kernel pinned (variant 6, or 8
+    with the iterate in tensor memory): its launches take the chains in the
+    order of their previous solve's iteration counts, which changes between
+    solves; the results do not depend on it (graph and eager bitwise equal,
+    and a chain's solution equal to that of the same chain solved alone)."""
     import paper_1512_03812_gb300 as P
     n = 160
     b = Batch([(64, 64)] * n, 2.0, 0.24, seed=14)
-    b.lat.set_cg_variant(6)
+    b.lat.set_cg_variant(variant)
     md = P.MD(scheme="adapted_nested_fg", tau=0.25, n=1, M=2,
               cg=P.CG(tol=1e-10, prec="mixed", delta=0.01), tol_action=1e-12)
     q0 = b.q()
@@ -95,7 +96,7 @@ def test_graph_equals_eager_longest_first(torch):
     assert torch.equal(qg, qe)
     # chain c's result is the same when it is solved alone
     one = Batch([(64, 64)], 2.0, 0.24, seed=14)
-    one.lat.set_cg_variant(6)
+    one.lat.set_cg_variant(variant)
     U64, U32 = b.lat.links(b.dev(q0))
     phi = b.dev(b.spinor())
     x, _, _ = b.lat.cg_solve(U64, U32, phi, P.CG(tol=1e-10, prec="mixed", delta=0.01))

@@ -152,7 +152,7 @@ def test_cg_layouts_agree(torch):
         assert rel_err(b.chain(xg, c), b.chain(xc, c)) < 1e-12
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 def test_chain_cg_kernel_variants_64x64(torch, variant):
     """Every kernel variant of the chain-resident mixed CG (strided, column
     512x8, column 256x16, two-block clusters, column pairs 512x4, 256x8 and in
@@ -201,7 +201,7 @@ def test_column_pair_variants_need_64x64_chains(torch):
     import paper_1512_03812_gb300 as P
     b = batch(torch, dims=[(32, 128)] * 2, betas=2.0, kappas=0.24, seed=3)
     b.lat.set_cg_variant(1)
-    for v in (5, 6, 7):
+    for v in (5, 6, 7, 8):
         with pytest.raises(P.SchwingerError):
             b.lat.set_cg_variant(v)
     q, phi = b.q(), b.spinor()
@@ -641,3 +641,22 @@ def test_mixed_delta_h_within_1e8_of_fp64_on_64x64(torch):
     assert np.abs(dHf).max() < 10.0, dHf  # a sensible trajectory
     assert np.abs(dHm - dHf).max() < 1e-8, np.abs(dHm - dHf).max()
     assert np.array_equal(accm, accf)
+
+
+def test_tmem_variant_is_bitwise_the_register_variant(torch):
+    """Variant 8 (x in tensor memory, the thread's own p in registers) does
+    the arithmetic of variant 6 in the same order: the same iteration counts
+    and bitwise the same solutions, on thermalisation-free hot links of
+    64 x 64 chains."""
+    import paper_1512_03812_gb300 as P
+    b = batch(torch, dims=[(64, 64)] * 4, betas=2.0, kappas=0.25, seed=17)
+    q, phi = b.q(), b.spinor()
+    U64, U32 = b.lat.links(b.dev(q))
+    out = {}
+    for v in (6, 8):
+        b.lat.set_cg_variant(v)
+        out[v] = b.lat.cg_solve(U64, U32, b.dev(phi),
+                                P.CG(tol=1e-10, prec="mixed", delta=0.01, algo="chain"))
+    assert np.array_equal(out[6][1], out[8][1]), (out[6][1], out[8][1])
+    assert torch.equal(out[6][0], out[8][0])
+    assert (out[8][2] <= 1e-10).all()
