@@ -605,16 +605,36 @@ __device__ __forceinline__ unsigned krank() {
 // below moves 16 consecutive 32-bit columns of that lane to or from 16
 // registers.  One warp allocates the columns of the block and frees them
 // before the block exits.
+// (the load and its wait in one statement: the registers are never read
+// before the data has arrived)
 __device__ __forceinline__ void tm_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
       "%11, %12, %13, %14, %15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
         "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
         "=r"(v[14]), "=r"(v[15])
       : "r"(taddr)
       : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+// An 8-column load left in flight (tm_wait8 completes it): issued one row
+// ahead of its use.  tm_wait8 takes the registers as operands, so nothing
+// that reads them can be scheduled before it.
+__device__ __forceinline__ void tm_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tm_wait8(uint32_t (&v)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                 "+r"(v[6]), "+r"(v[7])
+               :
+               : "memory");
 }
 __device__ __forceinline__ void tm_st16(uint32_t taddr, const uint32_t (&v)[16]) {
   asm volatile(
@@ -687,22 +707,25 @@ constexpr int pair_min_blocks() {
 // TM (one block, whole warpgroups): the FP32 iterate x, touched once per
 // iteration (x += alpha p in the p update, and at a reliable update), lives
 // in tensor memory instead of registers (the thread's 2 R sites in 8 R
-// columns of its warp's lane quarter).  The registers it leaves free hold
-// the thread's own p from the p update through the D walk and its own
-// t = D p from the D walk through the D^dag walk, so neither walk reads the
-// thread's own sites from shared memory (120 instead of 152 bytes of shared
-// memory per site-iteration).  The arithmetic and its order are those of
-// TM = false: the results are bitwise the same.  Keeping p in registers
-// across the D^dag walk as well spilled 364 bytes and was 11 % slower.
+// columns of its warp's lane quarter), and so do the thread's own links
+// (8 R more columns, written once; each walk loads a row's links one row
+// ahead of their use).  The registers x leaves free hold the thread's own p
+// from the p update through the D walk and its own t = D p from the D walk
+// through the D^dag walk, so neither walk reads the thread's own sites or
+// own links from shared memory (88 instead of 152 bytes of shared memory per
+// site-iteration).  The arithmetic and its order are those of TM = false:
+// the results are bitwise the same.  Keeping p in registers across the
+// D^dag walk as well spilled 364 bytes and was 11 % slower.
 template <int R, int NT, int L, int T, int K, bool TM = false>
 __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_pair(ChainCgArgs a) {
   static_assert(L % 2 == 0 && T % K == 0 && L * T == 2 * R * NT * K,
                 "one thread per two columns of R rows");
   static_assert(!TM || (K == 1 && NT % 128 == 0 && R % 2 == 0),
                 "TMEM form: one block, whole warpgroups, four sites per 16-column chunk");
-  // TMEM form: the thread's 2 R sites of x take 8 R columns; the warps of
+  // TMEM form: the thread's 2 R sites of x take 8 R columns, then its own
+  // links (U_x, U_t of its two sites, row by row) 8 R more; the warps of
   // one quarter take consecutive column groups
-  constexpr int TMC = 8 * R, TMG = NT / 128;
+  constexpr int TMC = 16 * R, TMG = NT / 128;
   constexpr uint32_t TMCOLS = TMC * TMG <= 32 ? 32 : (TMC * TMG <= 64 ? 64 : (TMC * TMG <= 128 ? 128 : (TMC * TMG <= 256 ? 256 : 512)));
   static_assert(NT % 32 == 0 && (T / K) % R == 0 && NT == (L / 2) * (T / K / R),
                 "whole warps; the threads tile the part's rows in strips of R");
@@ -803,6 +826,22 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
     const uint32_t zero[16] = {};
 #pragma unroll
     for (int ch = 0; ch < 2 * R / 4; ++ch) tm_st16(taddr + 16 * ch, zero);
+    // the links of rows 2 jj and 2 jj + 1, from this thread's own entries of
+    // shared memory
+#pragma unroll
+    for (int jj = 0; jj < R / 2; ++jj) {
+      uint32_t lk[16];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int row = (t0 + 2 * jj + h) * L;
+        const float2 ux0 = uxs[row + qe], ut0 = uts[row + qe], ux1 = uxs[row + qo],
+                     ut1 = uts[row + qo];
+        const float f[8] = {ux0.x, ux0.y, ut0.x, ut0.y, ux1.x, ux1.y, ut1.x, ut1.y};
+#pragma unroll
+        for (int m = 0; m < 8; ++m) lk[8 * h + m] = __float_as_uint(f[m]);
+      }
+      tm_st16(taddr + 8 * R + 16 * jj, lk);
+    }
     tm_wait_st();
   }
   const double bb = tsumd(bbl);
@@ -837,6 +876,13 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
     // the backward t-hops into row t0, then the rows' own hops
     Cx<float> ge = hop_tm<DAG, float>(cx(ubr[qe]), sp_of(fbr[qe]));
     Cx<float> go = hop_tm<DAG, float>(cx(ubr[qo]), sp_of(fbr[qo]));
+    // the thread's own links of the current row: from TMEM in the TMEM form,
+    // the next row's load in flight while the current one is computed
+    uint32_t lk[8], lkn[8];
+    if constexpr (TM) {
+      tm_ld8(taddr + 8 * R, lk);
+      tm_wait8(lk);
+    }
     Sp<float> fce, fco;
     if constexpr (OWN != 0) {
       fce = ownv(0);
@@ -861,8 +907,19 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
         fne = sp_of(far[qe]);
         fno = sp_of(far[qo]);
       }
-      const Cx<float> uxe = cx(uxs[row + qe]), ute = cx(uts[row + qe]);
-      const Cx<float> uxo = cx(uxs[row + qo]), uto = cx(uts[row + qo]);
+      Cx<float> uxe, ute, uxo, uto;
+      if constexpr (TM) {
+        if (j + 1 < R) tm_ld8(taddr + 8 * R + 8 * (j + 1), lkn);
+        uxe = {__uint_as_float(lk[0]), __uint_as_float(lk[1])};
+        ute = {__uint_as_float(lk[2]), __uint_as_float(lk[3])};
+        uxo = {__uint_as_float(lk[4]), __uint_as_float(lk[5])};
+        uto = {__uint_as_float(lk[6]), __uint_as_float(lk[7])};
+      } else {
+        uxe = cx(uxs[row + qe]);
+        ute = cx(uts[row + qe]);
+        uxo = cx(uxs[row + qo]);
+        uto = cx(uts[row + qo]);
+      }
       const Sp<float> oe =
           hop_sum_tm<DAG, float>(fco, sp_of(f[row + qm]), fne, uxe, cx(uxs[row + qm]), ute, ge);
       const Sp<float> oo = hop_sum_tm<DAG, float>(sp_of(f[row + qp]), fce, fno, uxo, uxe, uto, go);
@@ -871,6 +928,13 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
       go = hop_tm<DAG, float>(uto, fco);
       fce = fne;
       fco = fno;
+      if constexpr (TM) {
+        if (j + 1 < R) {
+          tm_wait8(lkn);
+#pragma unroll
+          for (int m = 0; m < 8; ++m) lk[m] = lkn[m];
+        }
+      }
       asm volatile("" ::: "memory");  // keep the next row's loads after this row
     }
   };
