@@ -73,15 +73,16 @@ SMEM_BYTES_PAIR = 2 * 16 + (64 + 40 + 32) // 2 + (64 + 40) // 2
 SMEM_BYTES_BY_VARIANT = ([SMEM_BYTES_STRIDED] + [SMEM_BYTES_COLUMN] * 2 + [SMEM_BYTES_CLUSTER] * 2
                          + [SMEM_BYTES_PAIR] * 4)
 # What actually crosses shared memory per site-iteration where it differs
-# from the layout's count: column pairs with x and the links in tensor
+# from the layout's count: column pairs with x, p and the links in tensor
 # memory (8) take the thread's own p in D, its own t in D^dag and its own 4
 # link halves from registers and TMEM, so per two sites D reads the two outer
 # x-neighbours (32) and one link half (8) and writes 2 (32), D^dag reads 2
-# neighbours and one link half, the p update 32: 88 B.  x and the links move
-# between TMEM and registers (32 + 32 B per site and iteration, not through
-# shared memory).  The roofline keeps the column pairs' 152 B (the operands
-# an iteration consumes from on-chip storage), so that the variants compare.
-SMEM_TRAFFIC_BY_VARIANT = {8: 32 + (32 + 8 + 32) // 2 + (32 + 8) // 2}
+# neighbours and one link half, the p update only writes p (16): 72 B.  x,
+# p and the links move between TMEM and registers (32 + 32 + 32 B per site
+# and iteration, not through shared memory).  The roofline keeps the column
+# pairs' 152 B (the operands an iteration consumes from on-chip storage), so
+# that the variants compare.
+SMEM_TRAFFIC_BY_VARIANT = {8: 16 + (32 + 8 + 32) // 2 + (32 + 8) // 2}
 # Shared-memory bandwidth per SM and clock (32 banks x 4 B).
 SMEM_BYTES_PER_CLK_PER_SM = 128
 NUM_SMS = 152

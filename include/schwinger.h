@@ -344,9 +344,9 @@ int sm_cg_solve(const sm_lattice* lat, const double* U64, const float* U32, cons
  * block per SM; 5: column pairs, 512 threads x 2 columns x 4 rows of 64 x 64
  * chains; 6: column pairs, 256 threads x 2 columns x 8 rows; 7: column pairs
  * split over a cluster of two blocks, 128 threads x 2 columns x 8 rows each;
- * 8: variant 6 with the FP32 iterate x and each thread's own links in
- * tensor memory (TMEM, 256 columns per block, allocated and freed by the
- * kernel) and, in the registers x leaves free, each thread's own p through
+ * 8: variant 6 with the FP32 iterate x, each thread's own p between
+ * iterations and its own links in tensor memory (TMEM, 512 columns per
+ * block, allocated and freed by the kernel) and, in the registers x leaves free, each thread's own p through
  * the D walk and own t = D p through the D^dag walk; the arithmetic of 6 in
  * the same order)
  * on the given solve (b, FP64; x is overwritten), and stores the fastest in the

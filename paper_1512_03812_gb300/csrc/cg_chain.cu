@@ -618,6 +618,23 @@ __device__ __forceinline__ void tm_ld16(uint32_t taddr, uint32_t (&v)[16]) {
       : "r"(taddr)
       : "memory");
 }
+// Two 16-column loads and their wait in one statement.
+__device__ __forceinline__ void tm_ld16x2(uint32_t ta, uint32_t (&a)[16], uint32_t tb,
+                                          uint32_t (&b)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
+      "%26, %27, %28, %29, %30, %31}, [%33];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]),
+        "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]),
+        "=r"(a[14]), "=r"(a[15]), "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]),
+        "=r"(b[5]), "=r"(b[6]), "=r"(b[7]), "=r"(b[8]), "=r"(b[9]), "=r"(b[10]), "=r"(b[11]),
+        "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15])
+      : "r"(ta), "r"(tb)
+      : "memory");
+}
 // An 8-column load left in flight (tm_wait8 completes it): issued one row
 // ahead of its use.  tm_wait8 takes the registers as operands, so nothing
 // that reads them can be scheduled before it.
@@ -709,11 +726,12 @@ constexpr int pair_min_blocks() {
 // in tensor memory instead of registers (the thread's 2 R sites in 8 R
 // columns of its warp's lane quarter), and so do the thread's own links
 // (8 R more columns, written once; each walk loads a row's links one row
-// ahead of their use).  The registers x leaves free hold the thread's own p
-// from the p update through the D walk and its own t = D p from the D walk
-// through the D^dag walk, so neither walk reads the thread's own sites or
-// own links from shared memory (88 instead of 152 bytes of shared memory per
-// site-iteration).  The arithmetic and its order are those of TM = false:
+// ahead of their use), and the thread's own p between iterations (8 R
+// more).  The registers x leaves free hold the thread's own p from the p
+// update through the D walk and its own t = D p from the D walk through the
+// D^dag walk, so neither walk nor the p update reads the thread's own sites
+// or own links from shared memory (72 instead of 152 bytes of shared memory
+// per site-iteration).  The arithmetic and its order are those of TM = false:
 // the results are bitwise the same.  Keeping p in registers across the
 // D^dag walk as well spilled 364 bytes and was 11 % slower.
 template <int R, int NT, int L, int T, int K, bool TM = false>
@@ -723,9 +741,9 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
   static_assert(!TM || (K == 1 && NT % 128 == 0 && R % 2 == 0),
                 "TMEM form: one block, whole warpgroups, four sites per 16-column chunk");
   // TMEM form: the thread's 2 R sites of x take 8 R columns, then its own
-  // links (U_x, U_t of its two sites, row by row) 8 R more; the warps of
-  // one quarter take consecutive column groups
-  constexpr int TMC = 16 * R, TMG = NT / 128;
+  // links (U_x, U_t of its two sites, row by row) 8 R more, then its own p
+  // 8 R more; the warps of one quarter take consecutive column groups
+  constexpr int TMC = 24 * R, TMG = NT / 128;
   constexpr uint32_t TMCOLS = TMC * TMG <= 32 ? 32 : (TMC * TMG <= 64 ? 64 : (TMC * TMG <= 128 ? 128 : (TMC * TMG <= 256 ? 256 : 512)));
   static_assert(NT % 32 == 0 && (T / K) % R == 0 && NT == (L / 2) * (T / K / R),
                 "whole warps; the threads tile the part's rows in strips of R");
@@ -825,7 +843,10 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
   if constexpr (TM) {
     const uint32_t zero[16] = {};
 #pragma unroll
-    for (int ch = 0; ch < 2 * R / 4; ++ch) tm_st16(taddr + 16 * ch, zero);
+    for (int ch = 0; ch < 2 * R / 4; ++ch) {
+      tm_st16(taddr + 16 * ch, zero);            // x = 0
+      tm_st16(taddr + 16 * R + 16 * ch, zero);   // p = 0
+    }
     // the links of rows 2 jj and 2 jj + 1, from this thread's own entries of
     // shared memory
 #pragma unroll
@@ -944,13 +965,15 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
     if constexpr (TM) {
 #pragma unroll
       for (int ch = 0; ch < 2 * R / 4; ++ch) {
-        uint32_t xr[16];
-        tm_ld16(taddr + 16 * ch, xr);
+        uint32_t xr[16], pr[16];
+        tm_ld16x2(taddr + 16 * ch, xr, taddr + 16 * R + 16 * ch, pr);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int i = 4 * ch + u;
           const int row = (t0 + i / 2) * L, q = row + ((i & 1) ? qo : qe);
-          const Sp<float> po = sp_of(ps[q]);
+          const Sp<float> po =
+              sp_of(make_float4(__uint_as_float(pr[4 * u]), __uint_as_float(pr[4 * u + 1]),
+                                __uint_as_float(pr[4 * u + 2]), __uint_as_float(pr[4 * u + 3])));
           const Sp<float> xs =
               sp_of(make_float4(__uint_as_float(xr[4 * u]), __uint_as_float(xr[4 * u + 1]),
                                 __uint_as_float(xr[4 * u + 2]), __uint_as_float(xr[4 * u + 3]))) +
@@ -961,8 +984,13 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
           xr[4 * u + 3] = __float_as_uint(xs.b.im);
           pv[i] = rv[i] + beta * po;
           ps[q] = f4_of(pv[i]);
+          pr[4 * u] = __float_as_uint(pv[i].a.re);
+          pr[4 * u + 1] = __float_as_uint(pv[i].a.im);
+          pr[4 * u + 2] = __float_as_uint(pv[i].b.re);
+          pr[4 * u + 3] = __float_as_uint(pv[i].b.im);
         }
         tm_st16(taddr + 16 * ch, xr);
+        tm_st16(taddr + 16 * R + 16 * ch, pr);
       }
       tm_wait_st();
     } else {
