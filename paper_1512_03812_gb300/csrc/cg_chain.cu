@@ -738,8 +738,8 @@ template <int R, int NT, int L, int T, int K, bool TM = false>
 __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_pair(ChainCgArgs a) {
   static_assert(L % 2 == 0 && T % K == 0 && L * T == 2 * R * NT * K,
                 "one thread per two columns of R rows");
-  static_assert(!TM || (K == 1 && NT % 128 == 0 && R % 2 == 0),
-                "TMEM form: one block, whole warpgroups, four sites per 16-column chunk");
+  static_assert(!TM || (NT % 128 == 0 && R % 2 == 0),
+                "TMEM form: whole warpgroups, four sites per 16-column chunk");
   // TMEM form: the thread's 2 R sites of x take 8 R columns, then its own
   // links (U_x, U_t of its two sites, row by row) 8 R more, then its own p
   // 8 R more; the warps of one quarter take consecutive column groups
@@ -1560,7 +1560,7 @@ int chain_cg_prepare(const sm_lattice* L, const sm_cg_params& cg) {
     e = cudaFuncSetAttribute(k_cg_chain_pair<8, 128, 64, 64, 2>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem / 2);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_cg_chain_pair<4, 256, 128, 128, 8>,
+    e = cudaFuncSetAttribute(k_cg_chain_pair<4, 256, 128, 128, 8, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 2048 * 16);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_cg_chain_pair<2, 64, 16, 16, 1>,
@@ -1636,6 +1636,10 @@ int chain_group_kind(const ChainInfo& ci) {
   }
 }
 
+// Tensor memory of the TMEM forms: 512 columns per block of the one-block
+// 64 x 64 kernel (192 KB of shared memory: alone on its SM), 256 per block
+// of the 8-block 128 x 128 clusters (96 KB: at most two on an SM); no other
+// kernel allocates it, so an allocation never waits.
 // Launches the mixed chain-resident solve of one kernel group on stream s,
 // the group's chains longest first (by their previous solve).  Column pairs
 // per shape (threads x rows per thread): 16 x 16: 64 x 2, 32 x 32: 128 x 4,
@@ -1671,7 +1675,7 @@ static int launch_group(Ctx& c, const ChainCgArgs& a0, int g, cudaStream_t s) {
     case 1: go(k_cg_chain_pair<2, 64, 16, 16, 1>, 64); break;
     case 2: go(k_cg_chain_pair<4, 128, 32, 32, 1>, 128); break;
     case 3: go(k_cg_chain_pair<4, 288, 48, 48, 1>, 288); break;
-    case 4: go(k_cg_chain_pair<8, 256, 64, 64, 1>, 256); break;
+    case 4: go(k_cg_chain_pair<8, 256, 64, 64, 1, true>, 256); break;
     default: {
       const int vmax = L->group_vmax[g];
       if (vmax <= 1024)
@@ -1765,7 +1769,7 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
       ab.list = c.w.order;
     }
     if (sq128)
-      e = launch_cluster<8>(k_cg_chain_pair<4, 256, 128, 128, 8>, L->nbig, 256,
+      e = launch_cluster<8>(k_cg_chain_pair<4, 256, 128, 128, 8, true>, L->nbig, 256,
                             (size_t)3 * 2048 * 16, c.s, ab);
     else
       e = launch_cluster<4>(k_cg_chain_cluster<8, 512, 4>, L->nbig, 512, (size_t)3 * 4096 * 16,
