@@ -90,6 +90,12 @@ NUM_SMS = 152
 # the committed ncu captures, keyed by kernel, with the sources they were
 # taken on: a changed source makes the figure stale (reported as null)
 NCU_CAPTURES = {
+    # the first solve of a step (S_F of H from the cold start, tolerance 1e-12,
+    # reliable-update factor 1e-3), one launch of 304 chains
+    "k_cg_chain_pair<8,256,64,64,1,true>": {
+        "sources": {"paper_1512_03812_gb300/csrc/cg_chain.cu": "089ae0f231be19cd",
+                    "paper_1512_03812_gb300/csrc/common.cuh": "e4b4838dd0c85c79"},
+        "dram_bytes_per_launch": 118262272 + 59806720},
     "k_cg_chain_pair<8,256,64,64,1>": {
         "sources": {"paper_1512_03812_gb300/csrc/cg_chain.cu": "108bcefb617db4c2",
                     "paper_1512_03812_gb300/csrc/common.cuh": "e4b4838dd0c85c79"},
@@ -671,8 +677,8 @@ OTHER_WORKLOADS = {
 
 
 BATCHED_KERNELS = {16: "k_cg_chain_pair<2,64,16,16,1>", 32: "k_cg_chain_pair<4,128,32,32,1>",
-                   48: "k_cg_chain_pair<4,288,48,48,1>", 64: "k_cg_chain_pair<8,256,64,64,1>",
-                   128: "k_cg_chain_pair<4,256,128,128,8> (8-block clusters)"}
+                   48: "k_cg_chain_pair<4,288,48,48,1>", 64: "k_cg_chain_pair<8,256,64,64,1,true>",
+                   128: "k_cg_chain_pair<4,256,128,128,8,true> (8-block clusters)"}
 
 
 def batched_kernels(torch, P, lat, q, Ls, betas, m0, cgp, smem_peak):

@@ -644,8 +644,8 @@ def test_mixed_delta_h_within_1e8_of_fp64_on_64x64(torch):
 
 
 def test_tmem_variant_is_bitwise_the_register_variant(torch):
-    """Variant 8 (x in tensor memory, the thread's own p in registers) does
-    the arithmetic of variant 6 in the same order: the same iteration counts
+    """Variant 8 (x, the thread's own links and its own p between iterations
+    in tensor memory) does the arithmetic of variant 6 in the same order: the same iteration counts
     and bitwise the same solutions, on thermalisation-free hot links of
     64 x 64 chains."""
     import paper_1512_03812_gb300 as P
