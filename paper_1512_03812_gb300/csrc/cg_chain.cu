@@ -752,6 +752,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
   __shared__ float red[2][NT / 32];
   __shared__ double redd[33];
   __shared__ float slot[2];  // this block's part of the two sums of an iteration
+  __shared__ float bsum[2];  // the two sums, over the cluster
   __shared__ double slotd;   // this block's part of an FP64 sum
   const unsigned rank = krank<K>();
   const int c = a.list[blockIdx.x / K];
@@ -797,11 +798,23 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if constexpr (K > 1) {
+      // the parts in rank order: lane j of warp 0 reads rank j's part (one
+      // distributed-shared-memory load a lane), the warp adds them in rank
+      // order and the sum reaches the block through bsum.  Barrier and sum
+      // took 0.56 us at K = 8 and 0.63 at 16 this way, 0.66 and 1.32 with
+      // every thread reading all K parts (the same additions in the same
+      // order: the same result)
       if (threadIdx.x == 0) slot[kk] = s;
       ksync<K>();
-      s = 0.f;
+      if (w == 0) {
+        const float v = lane < K ? kmap<K>(slot, lane)[kk] : 0.f;
+        float u = 0.f;
 #pragma unroll
-      for (int j = 0; j < K; ++j) s += kmap<K>(slot, j)[kk];
+        for (int j = 0; j < K; ++j) u += __shfl_sync(0xffffffffu, v, j);
+        if (lane == 0) bsum[kk] = u;
+      }
+      __syncthreads();
+      s = bsum[kk];
     }
     return s;
   };
@@ -1645,9 +1658,11 @@ int chain_group_kind(const ChainInfo& ci) {
 // per shape (threads x rows per thread): 16 x 16: 64 x 2, 32 x 32: 128 x 4,
 // 48 x 48: 288 x 4, 64 x 64: 256 x 8 (each 2 columns wide; at 64 x 64 the
 // 256 x 8 form solves faster than 512 x 4 also when its chain has the SM to
-// itself).  Other shapes: the strided kernel.  The kernel depends only on
-// the chain's shape, so a chain's result does not depend on the rest of its
-// batch.
+// itself, and faster than 4-block clusters of 128 x 4 once the group fills
+// the GPU: 2.7 against 4.8 ms for 304 chains, although the clusters take
+// 48 chains in 1.1 against 1.5 ms).  Other shapes: the strided kernel.  The
+// kernel depends only on the chain's shape, so a chain's result does not
+// depend on the rest of its batch.
 static int launch_group(Ctx& c, const ChainCgArgs& a0, int g, cudaStream_t s) {
   const sm_lattice* L = c.L;
   ChainCgArgs a = a0;
@@ -1747,7 +1762,7 @@ int chain_cg_launch(Ctx& c, const double* U64, const float* U32, const double* b
   const dim3 grid((unsigned)L->nchains), block(kChainThreads);
   (void)block;
   if (cg.prec == SM_MIXED && L->nbig > 0) {
-    // small chains on the side stream, 4-block clusters for the large ones
+    // small chains on the side stream, clusters for the large ones
     cudaError_t e = cudaEventRecord(L->ev_fork, c.s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(L->side, L->ev_fork, 0);
     if (e != cudaSuccess) return fail(SM_ERR_CUDA, "chain CG fork: %s", cudaGetErrorString(e));
