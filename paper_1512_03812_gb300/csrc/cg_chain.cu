@@ -365,6 +365,102 @@ struct ColWalk {
   }
 };
 
+// Double-float numbers for the intermediate reliable updates of the column
+// pairs: a value is the unevaluated sum h + l of two floats with |l| at most
+// half an ulp of h, about 48 significant bits (T. J. Dekker, "A
+// floating-point technique for extending the available precision", Numer.
+// Math. 18, 1971; the error-free sum of D. E. Knuth, TAOCP vol. 2, 4.2.2).
+// On GB300 the FP64 pipe runs at 1/64 of the FP32 rate, so a double-float
+// D^dag D of a chain costs a fraction of the FP64 one.  The operations are
+// written with explicit round-to-nearest intrinsics, which the compiler does
+// not fuse or reorder: the error-free transformations depend on it.
+struct Df {
+  float h, l;
+};
+// a + b = s + e exactly (Knuth)
+__device__ __forceinline__ Df df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// a + b = s + e exactly when |a| >= |b| (Dekker)
+__device__ __forceinline__ Df df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// the sum, with an error of order 2^-47 (|x| + |y|)
+__device__ __forceinline__ Df operator+(Df x, Df y) {
+  const Df s = df_two_sum(x.h, y.h);
+  return df_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
+}
+__device__ __forceinline__ Df operator-(Df x) { return {-x.h, -x.l}; }
+__device__ __forceinline__ Df operator-(Df x, Df y) { return x + (-y); }
+// the product: x.h y.h exactly as p + e (the fused multiply-add gives the
+// rounding error of p), plus the cross terms
+__device__ __forceinline__ Df operator*(Df x, Df y) {
+  const float p = __fmul_rn(x.h, y.h);
+  float e = __fmaf_rn(x.h, y.h, -p);
+  e = __fmaf_rn(x.h, y.l, e);
+  e = __fmaf_rn(x.l, y.h, e);
+  return df_fast_two_sum(p, e);
+}
+// the FP64 value v as h + l (v - h is exact in FP64)
+__device__ __forceinline__ Df df_of(double v) {
+  const float h = __double2float_rn(v);
+  return {h, __double2float_rn(v - (double)h)};
+}
+__device__ __forceinline__ Cx<Df> df_of(Cx<double> v) { return {df_of(v.re), df_of(v.im)}; }
+__device__ __forceinline__ Sp<Df> df_of(const Sp<double>& v) { return {df_of(v.a), df_of(v.b)}; }
+__device__ __forceinline__ float flt_of(Df x) { return __fadd_rn(x.h, x.l); }
+// half of a spinor (exact)
+__device__ __forceinline__ Sp<Df> df_half(const Sp<Df>& v) {
+  auto hf = [](Df x) { return Df{0.5f * x.h, 0.5f * x.l}; };
+  return {{hf(v.a.re), hf(v.a.im)}, {hf(v.b.re), hf(v.b.im)}};
+}
+// Double-float fields: 8 floats per site, (h, l) of a.re, a.im, b.re, b.im
+// for spinors and of U_x.re, U_x.im, U_t.re, U_t.im for links; they occupy
+// the 32 bytes per site of an FP64 spinor field.  Written in the same
+// kernel, so read at L2.
+__device__ __forceinline__ Sp<Df> ld_spdf(const float* f, long long n) {
+  const float4* q = reinterpret_cast<const float4*>(f) + 2 * SM_SITE(n);
+  const float4 u = __ldcg(q), v = __ldcg(q + 1);
+  return {{{u.x, u.y}, {u.z, u.w}}, {{v.x, v.y}, {v.z, v.w}}};
+}
+__device__ __forceinline__ void st_spdf(float* f, long long n, const Sp<Df>& s) {
+  float4* q = reinterpret_cast<float4*>(f) + 2 * SM_SITE(n);
+  q[0] = make_float4(s.a.re.h, s.a.re.l, s.a.im.h, s.a.im.l);
+  q[1] = make_float4(s.b.re.h, s.b.re.l, s.b.im.h, s.b.im.l);
+}
+__device__ __forceinline__ Lk<Df> ld_lkdf(const float* U, long long n) {
+  const Sp<Df> v = ld_spdf(U, n);
+  return {v.a, v.b};
+}
+__device__ __forceinline__ Cx<Df> ld_uxdf(const float* U, long long n) {
+  const float4 u = __ldcg(reinterpret_cast<const float4*>(U) + 2 * SM_SITE(n));
+  return {{u.x, u.y}, {u.z, u.w}};
+}
+
+// ColWalk in double-float arithmetic, on double-float copies of x_hi and of
+// the links (the same hops in the same order)
+struct ColWalkDf {
+  const float* U;
+  long long off;
+  int L, T, x, xp, xm, t0;
+  Df diag;
+  __device__ long long row(int t) const {
+    return off + (long long)(t < 0 ? t + T : (t >= T ? t - T : t)) * L;
+  }
+  template <bool DAG>
+  __device__ Sp<Df> site(const float* f, int j, const Sp<Df>& fm, const Sp<Df>& fc,
+                         const Sp<Df>& fn, Cx<Df>& utm) const {
+    const long long rw = row(t0 + j);
+    const Lk<Df> u = ld_lkdf(U, rw + x);
+    const Sp<Df> o = hop_sum<DAG, Df>(ld_spdf(f, rw + xp), ld_spdf(f, rw + xm), fn, fm, u.x,
+                                      ld_uxdf(U, rw + xm), u.t, utm);
+    utm = u.t;
+    return diag * fc - df_half(o);
+  }
+};
 
 // Column layout for chains whose shape matches the block: thread tid owns
 // column x = tid % L and the R consecutive rows t0 .. t0 + R - 1 of row block
@@ -836,6 +932,11 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
   // form keeps the thread's own p in registers (pv) and x in TMEM; the
   // other form x in registers (xv) and p in shared memory only.
   Sp<float> rv[2 * R], xv[TM ? 1 : 2 * R], pv[TM ? 2 * R : 1], tv[TM ? 2 * R : 1];
+  // double-float copies of the links and of x_hi, and D x_hi of an
+  // intermediate reliable update, in the FP64 scratch fields (32 bytes a site)
+  float* Udf = reinterpret_cast<float*>(a.p64);
+  float* xdf = reinterpret_cast<float*>(a.r64);
+  float* tdf = reinterpret_cast<float*>(a.t64);
   double bbl = 0.0;
 #pragma unroll
   for (int i = 0; i < 2 * R; ++i) {
@@ -843,6 +944,11 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
     const float4 u = __ldg(reinterpret_cast<const float4*>(a.U32) + base + l);
     uxs[q] = make_float2(u.x, u.y);
     uts[q] = make_float2(u.z, u.w);
+    {
+      // the double-float links of the intermediate reliable updates
+      const Lk<double> u64 = ld_lk(a.U64, base + l);
+      st_spdf(Udf, base + l, Sp<Df>{df_of(u64.x), df_of(u64.t)});
+    }
     const Sp<double> bv = ld_sp(a.b, base + l);
     bbl += norm2(bv);
     rv[i] = to_flt(bv);
@@ -1052,7 +1158,13 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
     }
     rmax = fmaxf(rmax, rr);
     if (rr <= tol2bb || rr < delta2 * rmax || it >= a.maxit) {
-      // reliable update: x_hi += x + alpha p, r = b - A x_hi in FP64
+      // reliable update: x_hi += x + alpha p, r = b - A x_hi.  An update
+      // that may end the solve (the iterated residual at the tolerance, or
+      // maxit) computes r in FP64, and the solve ends only on such an update
+      // (D x_hi, left in t64, is the caller's D x); the others only restart
+      // the FP32 recurrence and compute r in double-float, which is far more
+      // precise than that recurrence needs.
+      bool fin = rr <= tol2bb || it >= a.maxit;
       if constexpr (TM) {
 #pragma unroll
         for (int ch = 0; ch < 2 * R / 4; ++ch) {
@@ -1068,7 +1180,9 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
                                   __uint_as_float(xr[4 * u + 2]),
                                   __uint_as_float(xr[4 * u + 3]))) +
                 alpha * sp_of(ps[row + ((i & 1) ? qo : qe)]);
-            st_sp(a.x, n, ld_sp_cg(a.x, n) + to_dbl(xs));
+            const Sp<double> xn = ld_sp_cg(a.x, n) + to_dbl(xs);
+            st_sp(a.x, n, xn);
+            if (!fin) st_spdf(xdf, n, df_of(xn));
           }
           const uint32_t zero[16] = {};
           tm_st16(taddr + 16 * ch, zero);
@@ -1080,60 +1194,108 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
           const int row = (t0 + i / 2) * L;
           const long long n = base + row + 2 * k + (i & 1);
           const Sp<float> xs = xv[i] + alpha * sp_of(ps[row + ((i & 1) ? qo : qe)]);
-          st_sp(a.x, n, ld_sp_cg(a.x, n) + to_dbl(xs));
+          const Sp<double> xn = ld_sp_cg(a.x, n) + to_dbl(xs);
+          st_sp(a.x, n, xn);
+          if (!fin) st_spdf(xdf, n, df_of(xn));
           xv[i] = {{0.f, 0.f}, {0.f, 0.f}};
         }
       }
       alpha = 0.f;
-      ksync<K>();
-      {
+      for (;;) {
+        ksync<K>();
         // the walk down column 2k + s from the strip's first row in the chain
         const int tg = (int)rank * H + t0;
-        auto col = [&](int s) {
-          const int xs = 2 * k + s;
-          return ColWalk{a.U64, ci.off, L, T, xs, xs + 1 == L ? 0 : xs + 1, xs == 0 ? L - 1 : xs - 1,
-                         tg, 2.0 + ci.m0};
-        };
-        // t64 = D x_hi down both columns
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          const ColWalk cw = col(s);
-          Sp<double> fm = ld_sp_cg(a.x, cw.row(tg - 1) + cw.x), fc = ld_sp_cg(a.x, cw.row(tg) + cw.x);
-          Cx<double> utm = ld_lk(a.U64, cw.row(tg - 1) + cw.x).t;
-#pragma unroll 1
-          for (int j = 0; j < R; ++j) {
-            const Sp<double> fn = ld_sp_cg(a.x, cw.row(tg + j + 1) + cw.x);
-            st_sp(a.t64, cw.row(tg + j) + cw.x, cw.site<false>(a.x, j, fm, fc, fn, utm));
-            fm = fc;
-            fc = fn;
-          }
-        }
-        ksync<K>();
-        // r = b - D^dag t64 and |r|^2 (FP64); r goes to registers (FP32)
-        // through the thread's own sites of ts, free until the next D stage
         double v = 0.0;
+        if (!fin) {
+          const Df dg = df_of(2.0 + ci.m0);
+          auto cold = [&](int s) {
+            const int xs = 2 * k + s;
+            return ColWalkDf{Udf, ci.off, L, T, xs, xs + 1 == L ? 0 : xs + 1,
+                             xs == 0 ? L - 1 : xs - 1, tg, dg};
+          };
+          // D x_hi down both columns, in double-float
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          const ColWalk cw = col(s);
-          Sp<double> fm = ld_sp_cg(a.t64, cw.row(tg - 1) + cw.x), fc = ld_sp_cg(a.t64, cw.row(tg) + cw.x);
-          Cx<double> utm = ld_lk(a.U64, cw.row(tg - 1) + cw.x).t;
+          for (int s = 0; s < 2; ++s) {
+            const ColWalkDf cw = cold(s);
+            Sp<Df> fm = ld_spdf(xdf, cw.row(tg - 1) + cw.x), fc = ld_spdf(xdf, cw.row(tg) + cw.x);
+            Cx<Df> utm = ld_lkdf(Udf, cw.row(tg - 1) + cw.x).t;
+#pragma unroll 1
+            for (int j = 0; j < R; ++j) {
+              const Sp<Df> fn = ld_spdf(xdf, cw.row(tg + j + 1) + cw.x);
+              st_spdf(tdf, cw.row(tg + j) + cw.x, cw.site<false>(xdf, j, fm, fc, fn, utm));
+              fm = fc;
+              fc = fn;
+            }
+          }
+          ksync<K>();
+          // r = b - D^dag D x_hi, to FP32 through ts as below
 #pragma unroll
-          for (int j = 0; j < R; ++j) {
-            const Sp<double> fn = ld_sp_cg(a.t64, cw.row(tg + j + 1) + cw.x);
-            const Sp<double> r =
-                ld_sp(a.b, cw.row(tg + j) + cw.x) - cw.site<true>(a.t64, j, fm, fc, fn, utm);
-            v += norm2(r);
-            ts[(t0 + j) * L + (s ? qo : qe)] = f4_of(to_flt(r));
-            fm = fc;
-            fc = fn;
-            asm volatile("" ::: "memory");  // one row's loads at a time (registers)
+          for (int s = 0; s < 2; ++s) {
+            const ColWalkDf cw = cold(s);
+            Sp<Df> fm = ld_spdf(tdf, cw.row(tg - 1) + cw.x), fc = ld_spdf(tdf, cw.row(tg) + cw.x);
+            Cx<Df> utm = ld_lkdf(Udf, cw.row(tg - 1) + cw.x).t;
+#pragma unroll 1
+            for (int j = 0; j < R; ++j) {
+              const Sp<Df> fn = ld_spdf(tdf, cw.row(tg + j + 1) + cw.x);
+              const Sp<Df> rd = df_of(ld_sp(a.b, cw.row(tg + j) + cw.x)) -
+                                cw.site<true>(tdf, j, fm, fc, fn, utm);
+              const Sp<float> r{{flt_of(rd.a.re), flt_of(rd.a.im)}, {flt_of(rd.b.re), flt_of(rd.b.im)}};
+              v += (double)norm2(r);
+              ts[(t0 + j) * L + (s ? qo : qe)] = f4_of(r);
+              fm = fc;
+              fc = fn;
+            }
+          }
+        } else {
+          auto col = [&](int s) {
+            const int xs = 2 * k + s;
+            return ColWalk{a.U64, ci.off, L, T, xs, xs + 1 == L ? 0 : xs + 1, xs == 0 ? L - 1 : xs - 1,
+                           tg, 2.0 + ci.m0};
+          };
+          // t64 = D x_hi down both columns
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            const ColWalk cw = col(s);
+            Sp<double> fm = ld_sp_cg(a.x, cw.row(tg - 1) + cw.x), fc = ld_sp_cg(a.x, cw.row(tg) + cw.x);
+            Cx<double> utm = ld_lk(a.U64, cw.row(tg - 1) + cw.x).t;
+#pragma unroll 1
+            for (int j = 0; j < R; ++j) {
+              const Sp<double> fn = ld_sp_cg(a.x, cw.row(tg + j + 1) + cw.x);
+              st_sp(a.t64, cw.row(tg + j) + cw.x, cw.site<false>(a.x, j, fm, fc, fn, utm));
+              fm = fc;
+              fc = fn;
+            }
+          }
+          ksync<K>();
+          // r = b - D^dag t64 and |r|^2 (FP64); r goes to registers (FP32)
+          // through the thread's own sites of ts, free until the next D stage
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            const ColWalk cw = col(s);
+            Sp<double> fm = ld_sp_cg(a.t64, cw.row(tg - 1) + cw.x), fc = ld_sp_cg(a.t64, cw.row(tg) + cw.x);
+            Cx<double> utm = ld_lk(a.U64, cw.row(tg - 1) + cw.x).t;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+              const Sp<double> fn = ld_sp_cg(a.t64, cw.row(tg + j + 1) + cw.x);
+              const Sp<double> r =
+                  ld_sp(a.b, cw.row(tg + j) + cw.x) - cw.site<true>(a.t64, j, fm, fc, fn, utm);
+              v += norm2(r);
+              ts[(t0 + j) * L + (s ? qo : qe)] = f4_of(to_flt(r));
+              fm = fc;
+              fc = fn;
+              asm volatile("" ::: "memory");  // one row's loads at a time (registers)
+            }
           }
         }
         rr_true = tsumd(v);
 #pragma unroll
         for (int i = 0; i < 2 * R; ++i) rv[i] = sp_of(ts[(t0 + i / 2) * L + ((i & 1) ? qo : qe)]);
+        ++updates;
+        // a double-float update that finds the tolerance met is confirmed by
+        // an FP64 one (x_hi unchanged)
+        if (fin || !(rr_true <= a.tol2 * bb)) break;
+        fin = true;
       }
-      ++updates;
       if (!isfinite(rr_true)) {
         flags |= 2;
         break;
