@@ -123,7 +123,11 @@ typedef struct sm_lattice sm_lattice;
  * is tested, for SM_MIXED the FP64 true residual recomputed at each reliable
  * update.  A reliable update is taken when the FP32 residual has fallen by
  * the factor `delta` (0 < delta < 1) below its largest value since the last
- * one.  maxit bounds the iterations of every chain. */
+ * one.  In the chain-resident column-pair kernels an update that only
+ * restarts the FP32 recurrence computes the residual in double-float
+ * arithmetic (float pairs, about 48 bits); a solve ends only on an FP64
+ * update, whose true residual is the one tested.  maxit bounds the
+ * iterations of every chain. */
 typedef struct {
   double tol;
   int maxit;
