@@ -809,6 +809,99 @@ __device__ __forceinline__ void tm_free(uint32_t base, uint32_t ncols) {
 // slower: the FP32 iterate in global memory, updated by vector reductions at
 // L2 to free its registers (27 % slower), and the thread's own p kept in
 // registers besides shared memory (spills; 24 % slower).
+// The walks of a reliable update of the column pairs, each a function of
+// its own (not inlined: its registers do not weigh on the iteration loop's
+// allocation): D x_hi, then r = b - D^dag D x_hi on the thread's columns 2k
+// and 2k + 1 from row tg of the chain (t0 of the block's part), r to FP32
+// in the thread's own sites of ts; returns the thread's part of |r|^2.
+// Double-float form: on the float-pair copies of the links and of x_hi,
+// D x_hi to tdf, |r|^2 summed in FP32 (it only sets beta).
+template <int R, int L, int T, int K>
+__device__ __noinline__ double pair_update_df(const float* Udf, const float* xdf, float* tdf,
+                                              const double* b, long long off, double m0, int tg,
+                                              int t0, int k, int qe, int qo, float4* ts) {
+  const Df dg = df_of(2.0 + m0);
+  auto cold = [&](int s) {
+    const int xs = 2 * k + s;
+    return ColWalkDf{Udf, off, L, T, xs, xs + 1 == L ? 0 : xs + 1, xs == 0 ? L - 1 : xs - 1, tg, dg};
+  };
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const ColWalkDf cw = cold(s);
+    Sp<Df> fm = ld_spdf(xdf, cw.row(tg - 1) + cw.x), fc = ld_spdf(xdf, cw.row(tg) + cw.x);
+    Cx<Df> utm = ld_lkdf(Udf, cw.row(tg - 1) + cw.x).t;
+#pragma unroll 1
+    for (int j = 0; j < R; ++j) {
+      const Sp<Df> fn = ld_spdf(xdf, cw.row(tg + j + 1) + cw.x);
+      st_spdf(tdf, cw.row(tg + j) + cw.x, cw.site<false>(xdf, j, fm, fc, fn, utm));
+      fm = fc;
+      fc = fn;
+    }
+  }
+  ksync<K>();
+  float vf = 0.f;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const ColWalkDf cw = cold(s);
+    Sp<Df> fm = ld_spdf(tdf, cw.row(tg - 1) + cw.x), fc = ld_spdf(tdf, cw.row(tg) + cw.x);
+    Cx<Df> utm = ld_lkdf(Udf, cw.row(tg - 1) + cw.x).t;
+#pragma unroll 1
+    for (int j = 0; j < R; ++j) {
+      const Sp<Df> fn = ld_spdf(tdf, cw.row(tg + j + 1) + cw.x);
+      const Sp<Df> rd = df_of(ld_sp(b, cw.row(tg + j) + cw.x)) - cw.site<true>(tdf, j, fm, fc, fn, utm);
+      const Sp<float> r{{flt_of(rd.a.re), flt_of(rd.a.im)}, {flt_of(rd.b.re), flt_of(rd.b.im)}};
+      vf += norm2(r);
+      ts[(t0 + j) * L + (s ? qo : qe)] = f4_of(r);
+      fm = fc;
+      fc = fn;
+    }
+  }
+  return vf;
+}
+// FP64 form: t64 = D x_hi (the caller's D x when the solve ends here), |r|^2
+// in FP64.
+template <int R, int L, int T, int K>
+__device__ __noinline__ double pair_update_f64(const double* U64, const double* x, double* t64,
+                                               const double* b, long long off, double m0, int tg,
+                                               int t0, int k, int qe, int qo, float4* ts) {
+  auto col = [&](int s) {
+    const int xs = 2 * k + s;
+    return ColWalk{U64, off, L, T, xs, xs + 1 == L ? 0 : xs + 1, xs == 0 ? L - 1 : xs - 1, tg,
+                   2.0 + m0};
+  };
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const ColWalk cw = col(s);
+    Sp<double> fm = ld_sp_cg(x, cw.row(tg - 1) + cw.x), fc = ld_sp_cg(x, cw.row(tg) + cw.x);
+    Cx<double> utm = ld_lk(U64, cw.row(tg - 1) + cw.x).t;
+#pragma unroll 1
+    for (int j = 0; j < R; ++j) {
+      const Sp<double> fn = ld_sp_cg(x, cw.row(tg + j + 1) + cw.x);
+      st_sp(t64, cw.row(tg + j) + cw.x, cw.site<false>(x, j, fm, fc, fn, utm));
+      fm = fc;
+      fc = fn;
+    }
+  }
+  ksync<K>();
+  double v = 0.0;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const ColWalk cw = col(s);
+    Sp<double> fm = ld_sp_cg(t64, cw.row(tg - 1) + cw.x), fc = ld_sp_cg(t64, cw.row(tg) + cw.x);
+    Cx<double> utm = ld_lk(U64, cw.row(tg - 1) + cw.x).t;
+#pragma unroll 1
+    for (int j = 0; j < R; ++j) {
+      const Sp<double> fn = ld_sp_cg(t64, cw.row(tg + j + 1) + cw.x);
+      const Sp<double> r = ld_sp(b, cw.row(tg + j) + cw.x) - cw.site<true>(t64, j, fm, fc, fn, utm);
+      v += norm2(r);
+      ts[(t0 + j) * L + (s ? qo : qe)] = f4_of(to_flt(r));
+      fm = fc;
+      fc = fn;
+    }
+  }
+  return v;
+}
+
 // Blocks per SM the register budget is sized for: two where a block's part
 // of the chain takes at most half an SM's shared memory (clusters of parts
 // of 96 KB), else one.
@@ -1205,88 +1298,11 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
         ksync<K>();
         // the walk down column 2k + s from the strip's first row in the chain
         const int tg = (int)rank * H + t0;
-        double v = 0.0;
-        if (!fin) {
-          const Df dg = df_of(2.0 + ci.m0);
-          auto cold = [&](int s) {
-            const int xs = 2 * k + s;
-            return ColWalkDf{Udf, ci.off, L, T, xs, xs + 1 == L ? 0 : xs + 1,
-                             xs == 0 ? L - 1 : xs - 1, tg, dg};
-          };
-          // D x_hi down both columns, in double-float
-#pragma unroll
-          for (int s = 0; s < 2; ++s) {
-            const ColWalkDf cw = cold(s);
-            Sp<Df> fm = ld_spdf(xdf, cw.row(tg - 1) + cw.x), fc = ld_spdf(xdf, cw.row(tg) + cw.x);
-            Cx<Df> utm = ld_lkdf(Udf, cw.row(tg - 1) + cw.x).t;
-#pragma unroll 1
-            for (int j = 0; j < R; ++j) {
-              const Sp<Df> fn = ld_spdf(xdf, cw.row(tg + j + 1) + cw.x);
-              st_spdf(tdf, cw.row(tg + j) + cw.x, cw.site<false>(xdf, j, fm, fc, fn, utm));
-              fm = fc;
-              fc = fn;
-            }
-          }
-          ksync<K>();
-          // r = b - D^dag D x_hi, to FP32 through ts as below
-#pragma unroll
-          for (int s = 0; s < 2; ++s) {
-            const ColWalkDf cw = cold(s);
-            Sp<Df> fm = ld_spdf(tdf, cw.row(tg - 1) + cw.x), fc = ld_spdf(tdf, cw.row(tg) + cw.x);
-            Cx<Df> utm = ld_lkdf(Udf, cw.row(tg - 1) + cw.x).t;
-#pragma unroll 1
-            for (int j = 0; j < R; ++j) {
-              const Sp<Df> fn = ld_spdf(tdf, cw.row(tg + j + 1) + cw.x);
-              const Sp<Df> rd = df_of(ld_sp(a.b, cw.row(tg + j) + cw.x)) -
-                                cw.site<true>(tdf, j, fm, fc, fn, utm);
-              const Sp<float> r{{flt_of(rd.a.re), flt_of(rd.a.im)}, {flt_of(rd.b.re), flt_of(rd.b.im)}};
-              v += (double)norm2(r);
-              ts[(t0 + j) * L + (s ? qo : qe)] = f4_of(r);
-              fm = fc;
-              fc = fn;
-            }
-          }
-        } else {
-          auto col = [&](int s) {
-            const int xs = 2 * k + s;
-            return ColWalk{a.U64, ci.off, L, T, xs, xs + 1 == L ? 0 : xs + 1, xs == 0 ? L - 1 : xs - 1,
-                           tg, 2.0 + ci.m0};
-          };
-          // t64 = D x_hi down both columns
-#pragma unroll
-          for (int s = 0; s < 2; ++s) {
-            const ColWalk cw = col(s);
-            Sp<double> fm = ld_sp_cg(a.x, cw.row(tg - 1) + cw.x), fc = ld_sp_cg(a.x, cw.row(tg) + cw.x);
-            Cx<double> utm = ld_lk(a.U64, cw.row(tg - 1) + cw.x).t;
-#pragma unroll 1
-            for (int j = 0; j < R; ++j) {
-              const Sp<double> fn = ld_sp_cg(a.x, cw.row(tg + j + 1) + cw.x);
-              st_sp(a.t64, cw.row(tg + j) + cw.x, cw.site<false>(a.x, j, fm, fc, fn, utm));
-              fm = fc;
-              fc = fn;
-            }
-          }
-          ksync<K>();
-          // r = b - D^dag t64 and |r|^2 (FP64); r goes to registers (FP32)
-          // through the thread's own sites of ts, free until the next D stage
-#pragma unroll
-          for (int s = 0; s < 2; ++s) {
-            const ColWalk cw = col(s);
-            Sp<double> fm = ld_sp_cg(a.t64, cw.row(tg - 1) + cw.x), fc = ld_sp_cg(a.t64, cw.row(tg) + cw.x);
-            Cx<double> utm = ld_lk(a.U64, cw.row(tg - 1) + cw.x).t;
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-              const Sp<double> fn = ld_sp_cg(a.t64, cw.row(tg + j + 1) + cw.x);
-              const Sp<double> r =
-                  ld_sp(a.b, cw.row(tg + j) + cw.x) - cw.site<true>(a.t64, j, fm, fc, fn, utm);
-              v += norm2(r);
-              ts[(t0 + j) * L + (s ? qo : qe)] = f4_of(to_flt(r));
-              fm = fc;
-              fc = fn;
-              asm volatile("" ::: "memory");  // one row's loads at a time (registers)
-            }
-          }
-        }
+        double v;
+        if (!fin)
+          v = pair_update_df<R, L, T, K>(Udf, xdf, tdf, a.b, ci.off, ci.m0, tg, t0, k, qe, qo, ts);
+        else
+          v = pair_update_f64<R, L, T, K>(a.U64, a.x, a.t64, a.b, ci.off, ci.m0, tg, t0, k, qe, qo, ts);
         rr_true = tsumd(v);
 #pragma unroll
         for (int i = 0; i < 2 * R; ++i) rv[i] = sp_of(ts[(t0 + i / 2) * L + ((i & 1) ? qo : qe)]);
