@@ -404,10 +404,26 @@ __device__ __forceinline__ Df operator*(Df x, Df y) {
   e = __fmaf_rn(x.l, y.h, e);
   return df_fast_two_sum(p, e);
 }
-// the FP64 value v as h + l (v - h is exact in FP64)
+// v truncated to 24 significant bits, as a float, built from v's bits
+// (GB300 converts FP64 to FP32 at about half its FP64 add rate; integer
+// operations run at the full rate).  Magnitudes below the normal float
+// range give 0, above it (and inf, NaN) an infinity.
+__device__ __forceinline__ float flt_trunc(double v) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(v));
+  const unsigned hi = (unsigned)(u >> 32);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  const unsigned m = ((hi & 0xfffffu) << 3) | (unsigned)((u >> 29) & 7u);
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned)e << 23) | m);
+}
+// the FP64 value v as h + l: h is v truncated to a float, v - h is exact in
+// FP64 and truncated in turn (h + l within 2^-46 |v| of v; where l would
+// fall below the normal float range, within about 1e-38 of it)
 __device__ __forceinline__ Df df_of(double v) {
-  const float h = __double2float_rn(v);
-  return {h, __double2float_rn(v - (double)h)};
+  const float h = flt_trunc(v);
+  return {h, flt_trunc(v - (double)h)};
 }
 __device__ __forceinline__ Cx<Df> df_of(Cx<double> v) { return {df_of(v.re), df_of(v.im)}; }
 __device__ __forceinline__ Sp<Df> df_of(const Sp<double>& v) { return {df_of(v.a), df_of(v.b)}; }
@@ -809,6 +825,56 @@ __device__ __forceinline__ void tm_free(uint32_t base, uint32_t ncols) {
 // slower: the FP32 iterate in global memory, updated by vector reductions at
 // L2 to free its registers (27 % slower), and the thread's own p kept in
 // registers besides shared memory (spills; 24 % slower).
+// The float-pair copy of the thread's own links (once per solve), not
+// inlined for the same reason as the update walks below.
+template <int R, int L>
+__device__ __noinline__ void pair_split_links(const double* U64, float* Udf, long long base, int t0,
+                                              int k) {
+#pragma unroll 1
+  for (int i = 0; i < 2 * R; ++i) {
+    const long long n = base + (t0 + i / 2) * L + 2 * k + (i & 1);
+    const Lk<double> u = ld_lk(U64, n);
+    st_spdf(Udf, n, Sp<Df>{df_of(u.x), df_of(u.t)});
+  }
+}
+
+// The TMEM form's x_hi += x + alpha p at a reliable update (x from tensor
+// memory, zeroed after; p from shared memory), with the float-pair copy of
+// x_hi when the update is a double-float one.  Four sites' x_hi are loaded
+// before any is stored, so the loads overlap.
+template <int R, int L>
+__device__ __noinline__ void pair_update_x_tm(uint32_t taddr, const float4* ps, float alpha,
+                                              double* x, float* xdf, bool fin, long long base,
+                                              int t0, int k, int qe, int qo) {
+#pragma unroll 1
+  for (int ch = 0; ch < 2 * R / 4; ++ch) {
+    uint32_t xr[16];
+    tm_ld16(taddr + 16 * ch, xr);
+    Sp<double> xo[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = 4 * ch + u;
+      xo[u] = ld_sp_cg(x, base + (t0 + i / 2) * L + 2 * k + (i & 1));
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = 4 * ch + u;
+      const int row = (t0 + i / 2) * L;
+      const long long n = base + row + 2 * k + (i & 1);
+      const Sp<float> xs =
+          sp_of(make_float4(__uint_as_float(xr[4 * u]), __uint_as_float(xr[4 * u + 1]),
+                            __uint_as_float(xr[4 * u + 2]), __uint_as_float(xr[4 * u + 3]))) +
+          alpha * sp_of(ps[row + ((i & 1) ? qo : qe)]);
+      const Sp<double> xn = xo[u] + to_dbl(xs);
+      st_sp(x, n, xn);
+      if (!fin) st_spdf(xdf, n, df_of(xn));
+    }
+    const uint32_t zero[16] = {};
+    tm_st16(taddr + 16 * ch, zero);
+  }
+  tm_wait_st();
+}
+
 // The walks of a reliable update of the column pairs, each a function of
 // its own (not inlined: its registers do not weigh on the iteration loop's
 // allocation): D x_hi, then r = b - D^dag D x_hi on the thread's columns 2k
@@ -1037,11 +1103,6 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
     const float4 u = __ldg(reinterpret_cast<const float4*>(a.U32) + base + l);
     uxs[q] = make_float2(u.x, u.y);
     uts[q] = make_float2(u.z, u.w);
-    {
-      // the double-float links of the intermediate reliable updates
-      const Lk<double> u64 = ld_lk(a.U64, base + l);
-      st_spdf(Udf, base + l, Sp<Df>{df_of(u64.x), df_of(u64.t)});
-    }
     const Sp<double> bv = ld_sp(a.b, base + l);
     bbl += norm2(bv);
     rv[i] = to_flt(bv);
@@ -1052,6 +1113,8 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
     ps[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     st_sp(a.x, base + l, Sp<double>{{0, 0}, {0, 0}});
   }
+  // the double-float links of the intermediate reliable updates
+  pair_split_links<R, L>(a.U64, Udf, base, t0, k);
   if constexpr (TM) {
     const uint32_t zero[16] = {};
 #pragma unroll
@@ -1259,38 +1322,28 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
       // precise than that recurrence needs.
       bool fin = rr <= tol2bb || it >= a.maxit;
       if constexpr (TM) {
-#pragma unroll
-        for (int ch = 0; ch < 2 * R / 4; ++ch) {
-          uint32_t xr[16];
-          tm_ld16(taddr + 16 * ch, xr);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int i = 4 * ch + u;
-            const int row = (t0 + i / 2) * L;
-            const long long n = base + row + 2 * k + (i & 1);
-            const Sp<float> xs =
-                sp_of(make_float4(__uint_as_float(xr[4 * u]), __uint_as_float(xr[4 * u + 1]),
-                                  __uint_as_float(xr[4 * u + 2]),
-                                  __uint_as_float(xr[4 * u + 3]))) +
-                alpha * sp_of(ps[row + ((i & 1) ? qo : qe)]);
-            const Sp<double> xn = ld_sp_cg(a.x, n) + to_dbl(xs);
-            st_sp(a.x, n, xn);
-            if (!fin) st_spdf(xdf, n, df_of(xn));
-          }
-          const uint32_t zero[16] = {};
-          tm_st16(taddr + 16 * ch, zero);
-        }
-        tm_wait_st();
+        pair_update_x_tm<R, L>(taddr, ps, alpha, a.x, xdf, fin, base, t0, k, qe, qo);
       } else {
 #pragma unroll
-        for (int i = 0; i < 2 * R; ++i) {
-          const int row = (t0 + i / 2) * L;
-          const long long n = base + row + 2 * k + (i & 1);
-          const Sp<float> xs = xv[i] + alpha * sp_of(ps[row + ((i & 1) ? qo : qe)]);
-          const Sp<double> xn = ld_sp_cg(a.x, n) + to_dbl(xs);
-          st_sp(a.x, n, xn);
-          if (!fin) st_spdf(xdf, n, df_of(xn));
-          xv[i] = {{0.f, 0.f}, {0.f, 0.f}};
+        for (int c4 = 0; c4 < 2 * R; c4 += 4) {
+          // four sites' x_hi loaded before any is stored (the loads overlap)
+          Sp<double> xo[4];
+#pragma unroll
+          for (int u = 0; u < 4 && c4 + u < 2 * R; ++u) {
+            const int i = c4 + u;
+            xo[u] = ld_sp_cg(a.x, base + (t0 + i / 2) * L + 2 * k + (i & 1));
+          }
+#pragma unroll
+          for (int u = 0; u < 4 && c4 + u < 2 * R; ++u) {
+            const int i = c4 + u;
+            const int row = (t0 + i / 2) * L;
+            const long long n = base + row + 2 * k + (i & 1);
+            const Sp<float> xs = xv[i] + alpha * sp_of(ps[row + ((i & 1) ? qo : qe)]);
+            const Sp<double> xn = xo[u] + to_dbl(xs);
+            st_sp(a.x, n, xn);
+            if (!fin) st_spdf(xdf, n, df_of(xn));
+            xv[i] = {{0.f, 0.f}, {0.f, 0.f}};
+          }
         }
       }
       alpha = 0.f;
