@@ -1004,7 +1004,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
                 "whole warps; the threads tile the part's rows in strips of R");
   constexpr int H = T / K, V = H * L, HL = L / 2;  // rows and sites of a block's part
   extern __shared__ float4 smem[];
-  __shared__ float red[2][NT / 32];
+  __shared__ __align__(16) float red[2][NT / 32];
   __shared__ double redd[33];
   __shared__ float slot[2];  // this block's part of the two sums of an iteration
   __shared__ float bsum[2];  // the two sums, over the cluster
@@ -1049,9 +1049,19 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) red[kk][w] = v;
     __syncthreads();
-    float s = lane < NT / 32 ? red[kk][lane] : 0.f;
+    float s;
+    if constexpr (NT / 32 == 8) {
+      // the eight warp sums read as two 16-byte words and added in the
+      // pairing of the butterfly below (whose first two steps add zeros):
+      // the same sum, without five dependent shuffles
+      const float4 lo = reinterpret_cast<const float4*>(red[kk])[0];
+      const float4 hi = reinterpret_cast<const float4*>(red[kk])[1];
+      s = ((lo.x + hi.x) + (lo.z + hi.z)) + ((lo.y + hi.y) + (lo.w + hi.w));
+    } else {
+      s = lane < NT / 32 ? red[kk][lane] : 0.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
     if constexpr (K > 1) {
       // the parts in rank order: lane j of warp 0 reads rank j's part (one
       // distributed-shared-memory load a lane), the warp adds them in rank
