@@ -1111,8 +1111,10 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
   for (int i = 0; i < 2 * R; ++i) {
     const int row = (t0 + i / 2) * L, l = row + 2 * k + (i & 1), q = row + ((i & 1) ? qo : qe);
     const float4 u = __ldg(reinterpret_cast<const float4*>(a.U32) + base + l);
-    uxs[q] = make_float2(u.x, u.y);
-    uts[q] = make_float2(u.z, u.w);
+    // the links times -1/2 (exact): the hop sum then comes out as -o/2, and
+    // a site's result diag f - o/2 is one fused multiply-add per component
+    uxs[q] = make_float2(-0.5f * u.x, -0.5f * u.y);
+    uts[q] = make_float2(-0.5f * u.z, -0.5f * u.w);
     const Sp<double> bv = ld_sp(a.b, base + l);
     bbl += norm2(bv);
     rv[i] = to_flt(bv);
@@ -1229,7 +1231,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<L, T, K>())) k_cg_chain_p
       const Sp<float> oe =
           hop_sum_tm<DAG, float>(fco, sp_of(f[row + qm]), fne, uxe, cx(uxs[row + qm]), ute, ge);
       const Sp<float> oo = hop_sum_tm<DAG, float>(sp_of(f[row + qp]), fce, fno, uxo, uxe, uto, go);
-      emit(j, diag * fce - 0.5f * oe, diag * fco - 0.5f * oo);
+      emit(j, diag * fce + oe, diag * fco + oo);
       ge = hop_tm<DAG, float>(ute, fce);
       go = hop_tm<DAG, float>(uto, fco);
       fce = fne;
