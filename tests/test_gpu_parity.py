@@ -660,3 +660,30 @@ def test_tmem_variant_is_bitwise_the_register_variant(torch):
     assert np.array_equal(out[6][1], out[8][1]), (out[6][1], out[8][1])
     assert torch.equal(out[6][0], out[8][0])
     assert (out[8][2] <= 1e-10).all()
+
+
+@pytest.mark.parametrize("variant", [8, -1])
+def test_pair_kernels_force_uses_the_final_fp64_update(torch, variant):
+    """The column-pair kernels take the intermediate reliable updates in
+    double-float and end every solve on an FP64 one, whose D x_hi the fermion
+    force uses as chi = D xi.  On 64 x 64 chains (variant 8 pinned, and the
+    shape group's kernel when no variant is pinned) the solution meets the
+    FP64 true residual and the force agrees with the oracle's."""
+    import paper_1512_03812_gb300 as P
+    b = batch(torch, dims=[(64, 64)] * 2, betas=2.0, kappas=0.25, seed=29)
+    b.lat.set_cg_variant(variant)
+    q, eta = b.q(), b.eta()
+    qd = b.dev(q)
+    U64, U32 = b.lat.links(qd)
+    phi = b.lat.apply_D(U64, b.dev(eta), dagger=True)
+    cgm = P.CG(tol=1e-13, maxit=50000, prec="mixed", delta=3e-4, algo="chain")
+    x, _, relres = b.lat.cg_solve(U64, U32, phi, cgm)
+    assert (relres <= 1e-13).all(), relres
+    r = phi - b.lat.apply_DdagD(U64, x)
+    Ff = b.lat.fermion_force(qd, phi, cgm)
+    for c, ol in enumerate(b.olat):
+        assert np.linalg.norm(b.chain(r, c)) <= 1.0000001e-13 * np.linalg.norm(b.chain(phi, c))
+        U = sw.links(b.chain(q, c))
+        ph = sw.apply_D(ol, U, b.chain(eta, c), dagger=True)
+        Fo = sw.fermion_force(ol, U, ph, sw.Solver(1e-14))
+        assert rel_err(b.chain(Ff, c), Fo) < 1e-9, rel_err(b.chain(Ff, c), Fo)
