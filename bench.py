@@ -93,7 +93,7 @@ NCU_CAPTURES = {
     # the first solve of a step (S_F of H from the cold start, tolerance 1e-12,
     # reliable-update factor 1e-3), one launch of 304 chains
     "k_cg_chain_pair<8,256,64,64,1,true>": {
-        "sources": {"paper_1512_03812_gb300/csrc/cg_chain.cu": "536a0e4e220d36fa",
+        "sources": {"paper_1512_03812_gb300/csrc/cg_chain.cu": "8b7d70f02c100029",
                     "paper_1512_03812_gb300/csrc/common.cuh": "e4b4838dd0c85c79"},
         "dram_bytes_per_launch": 250515456 + 265532160},
     "k_cg_chain_pair<8,256,64,64,1>": {

@@ -366,10 +366,11 @@ struct ColWalk {
 };
 
 // Double-float numbers for the intermediate reliable updates of the column
-// pairs: a value is the unevaluated sum h + l of two floats with |l| at most
-// half an ulp of h, about 48 significant bits (T. J. Dekker, "A
-// floating-point technique for extending the available precision", Numer.
-// Math. 18, 1971; the error-free sum of D. E. Knuth, TAOCP vol. 2, 4.2.2).
+// pairs: a value is the unevaluated sum h + l of two floats with |l| below
+// an ulp of h (half an ulp after an operation), about 47 significant bits
+// (T. J. Dekker, "A floating-point technique for extending the available
+// precision", Numer. Math. 18, 1971; the error-free sum of D. E. Knuth,
+// TAOCP vol. 2, 4.2.2).
 // On GB300 the FP64 pipe runs at 1/64 of the FP32 rate, so a double-float
 // D^dag D of a chain costs a fraction of the FP64 one.  The operations are
 // written with explicit round-to-nearest intrinsics, which the compiler does
